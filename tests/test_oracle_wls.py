@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle (CPU only) against what the paper and the
+mathematics fix: paper-printed counts, closed forms, an independent complex
+power-flow formulation, finite differences, library least squares, brute
+force on tiny grids and the chi-square law of the WLS residual."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+from oracle import wls
+from paper_2604_23175_gb300 import synth
+from tests.helpers import net_of, problem, tiny_grid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")
+
+
+def _complex_flows(net, Vm, Va):
+    """Independent formulation: S_ij = V_i conj(I_ij), pi model, complex."""
+    V = Vm * np.exp(1j * Va)
+    y = 1.0 / (net.r + 1j * net.x)
+    ysh = 0.5j * net.b_charge
+    f, t = net.from_bus, net.to_bus
+    If = y * (V[f] - V[t]) + ysh * V[f]
+    It = y * (V[t] - V[f]) + ysh * V[t]
+    return V[f] * np.conj(If), V[t] * np.conj(It)
+
+
+def _ybus_injection(net, Vm, Va):
+    """Independent formulation: S = V conj(Ybus V)."""
+    N = net.n_bus
+    Y = np.zeros((N, N), dtype=complex)
+    y = 1.0 / (net.r + 1j * net.x)
+    for l in range(net.n_branch):
+        i, j = net.from_bus[l], net.to_bus[l]
+        Y[i, i] += y[l] + 0.5j * net.b_charge[l]
+        Y[j, j] += y[l] + 0.5j * net.b_charge[l]
+        Y[i, j] -= y[l]
+        Y[j, i] -= y[l]
+    V = Vm * np.exp(1j * Va)
+    return V * np.conj(Y @ V)
+
+
+def test_paper_counts_golden():
+    """n = 2N - 1 and m = 3N + 4L, one flow family = L rows = 17.01 % (Sec. 5.2, Table 3)."""
+    gold = json.load(open(GOLDEN))["pegase2869"]
+    grid = synth.make_grid("grid2869_k16")
+    assert grid.n_bus == gold["n_bus"] and grid.n_branch == gold["n_branch"]
+    net = net_of(grid)
+    H = wls.jacobian(net, *wls.flat_start(net))
+    assert H.shape == (3 * gold["n_bus"] + 4 * gold["n_branch"], gold["n_state"])
+    assert round(100.0 * gold["flow_family_rows"] / H.shape[0], 2) == gold["flow_family_fraction_percent"]
+    assert synth.family_mask(grid, "Pf").sum() == H.shape[0] - gold["flow_family_rows"]
+
+
+def test_boundary_dimension_rule():
+    """343 boundary variables for 172 boundary buses: the slack angle is dropped
+    when the slack is a boundary bus (Sec. 5.2); otherwise 2 per bus."""
+    gold = json.load(open(GOLDEN))["pegase2869"]
+    assert gold["boundary_variables"] == 2 * gold["boundary_buses"] - 1
+    for on_b in (False, True):
+        grid = synth.make_grid("grid2869_k16", slack_on_boundary=on_b)
+        net = net_of(grid)
+        part = wls.partition(net, grid.area_of_bus, grid.n_area)
+        nb = len(part.boundary_buses)
+        assert (0 in set(part.boundary_buses.tolist())) == on_b
+        assert len(part.gamma_cols) == 2 * nb - (1 if on_b else 0)
+
+
+def test_printed_objective_is_half_weighted_norm_squared():
+    """Reading of the objective scale: the printed objective equals half the
+    squared weighted residual norm for all three cases (Sec. 5.3)."""
+    for row in json.load(open(GOLDEN))["solution_agreement"]:
+        half = 0.5 * row["weighted_residual_norm"] ** 2
+        # norm printed to 2 decimals: |d(n^2/2)| <= n * 0.005
+        assert abs(half - row["objective"]) <= row["weighted_residual_norm"] * 0.005 + 0.01
+
+
+def test_flat_start_closed_form():
+    """V = 1, theta = 0: P_ij = g - g = 0 and Q_ij = -b_c / 2 at both ends."""
+    grid = synth.make_grid("grid300_k4")
+    net = net_of(grid)
+    Pf, Qf, Pt, Qt = wls.branch_flows(net, *wls.flat_start(net))
+    np.testing.assert_allclose(Pf, 0.0, atol=1e-13)
+    np.testing.assert_allclose(Pt, 0.0, atol=1e-13)
+    np.testing.assert_allclose(Qf, -0.5 * net.b_charge, atol=1e-13)
+    np.testing.assert_allclose(Qt, -0.5 * net.b_charge, atol=1e-13)
+
+
+def test_measurements_match_complex_power_flow():
+    grid = synth.make_grid("grid300_k4")
+    net = net_of(grid)
+    Vm, Va = synth.make_states(grid, 1, 11)
+    h = wls.measure(net, Vm[0], Va[0])
+    N, L = net.n_bus, net.n_branch
+    Sf, St = _complex_flows(net, Vm[0], Va[0])
+    Sinj = _ybus_injection(net, Vm[0], Va[0])
+    np.testing.assert_allclose(h[:N], Vm[0], rtol=0, atol=0)
+    np.testing.assert_allclose(h[N:2 * N], Sinj.real, atol=1e-10)
+    np.testing.assert_allclose(h[2 * N:3 * N], Sinj.imag, atol=1e-10)
+    o = 3 * N
+    np.testing.assert_allclose(h[o:o + L], Sf.real, atol=1e-11)
+    np.testing.assert_allclose(h[o + L:o + 2 * L], Sf.imag, atol=1e-11)
+    np.testing.assert_allclose(h[o + 2 * L:o + 3 * L], St.real, atol=1e-11)
+    np.testing.assert_allclose(h[o + 3 * L:o + 4 * L], St.imag, atol=1e-11)
+
+
+def test_jacobian_matches_central_differences():
+    grid = synth.make_grid("grid300_k4")
+    net = net_of(grid)
+    Vm, Va = synth.make_states(grid, 1, 12)
+    Vm, Va = Vm[0], Va[0]
+    H = wls.jacobian_full(net, Vm, Va).toarray()
+    N = net.n_bus
+    eps = 1e-6
+    rng = np.random.Generator(np.random.PCG64(3))
+    cols = rng.choice(2 * N, size=60, replace=False)
+    for c in cols:
+        dv = np.zeros(2 * N)
+        dv[c] = eps
+        hp = wls.measure(net, Vm + dv[:N], Va + dv[N:])
+        hm = wls.measure(net, Vm - dv[:N], Va - dv[N:])
+        fd = (hp - hm) / (2 * eps)
+        scale = max(1.0, np.max(np.abs(H[:, c])))
+        assert np.max(np.abs(fd - H[:, c])) <= 1e-6 * scale, c
+
+
+def test_noise_free_measurements_recover_state():
+    grid = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(grid, 1, 2100, noise=False)
+    w = wls.weights(sig)
+    res = wls.gauss_newton(net, z[0], w, tol=1e-12, max_iter=20)
+    assert res.converged
+    assert np.max(np.abs(res.Vm - Vm[0])) < 1e-10
+    assert np.max(np.abs(res.Va - Va[0])) < 1e-10
+    part = wls.partition(net, grid.area_of_bus, grid.n_area)
+    res2 = wls.multi_area_gauss_newton(net, part, z[0], w, tol=1e-12, max_iter=20)
+    assert np.max(np.abs(res2.Vm - Vm[0])) < 1e-10
+    assert np.max(np.abs(res2.Va - Va[0])) < 1e-10
+
+
+def test_gradient_vanishes_at_solution():
+    grid = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(grid, 1, 2200)
+    w = wls.weights(sig)
+    res = wls.gauss_newton(net, z[0], w, tol=1e-12, max_iter=20)
+    G, g = wls.gain_and_gradient(net, z[0], w, res.Vm, res.Va)
+    # first-order optimality relative to the size of the gradient at flat start
+    _, g0 = wls.gain_and_gradient(net, z[0], w, *wls.flat_start(net))
+    assert np.max(np.abs(g)) < 1e-9 * np.max(np.abs(g0))
+    assert np.all(np.linalg.eigvalsh(G) > 0)
+
+
+def test_minimiser_matches_library_least_squares_with_complex_model():
+    """Brute-force check of the GN minimiser on a tiny grid: minimise the WLS
+    objective with SciPy's trust-region least squares over a residual built
+    from the complex power-flow formulation (no oracle arithmetic)."""
+    grid = tiny_grid(8, 2, seed=3)
+    net, Vm, Va, z, sig = problem(grid, 1, 2300)
+    w = wls.weights(sig)
+    N, L = net.n_bus, net.n_branch
+
+    def resid(xv):
+        vm = xv[:N]
+        va = np.concatenate([[0.0], xv[N:]])
+        Sf, St = _complex_flows(net, vm, va)
+        Si = _ybus_injection(net, vm, va)
+        h = np.concatenate([vm, Si.real, Si.imag, Sf.real, Sf.imag, St.real, St.imag])
+        return np.sqrt(w) * (z[0] - h)
+
+    x0 = np.concatenate([np.ones(N), np.zeros(N - 1)])
+    ls = so.least_squares(resid, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, method="trf")
+    res = wls.gauss_newton(net, z[0], w, tol=1e-13, max_iter=30)
+    np.testing.assert_allclose(res.Vm, ls.x[:N], atol=1e-8)
+    np.testing.assert_allclose(res.Va[1:], ls.x[N:], atol=1e-8)
+    assert abs(res.J - 2 * ls.cost) <= 1e-9 * max(1.0, res.J)
+
+
+@pytest.mark.parametrize("slack_on_boundary", [False, True])
+def test_schur_step_equals_dense_solve_on_tiny_grid(slack_on_boundary):
+    """Block elimination is exact: the condensed step equals G^{-1} H^T W r."""
+    grid = tiny_grid(12, 3, seed=5, slack_on_boundary=slack_on_boundary)
+    net, Vm, Va, z, sig = problem(grid, 1, 2400)
+    w = wls.weights(sig)
+    part = wls.partition(net, grid.area_of_bus, grid.n_area)
+    assert (0 in set(part.boundary_buses.tolist())) == slack_on_boundary
+    rng = np.random.Generator(np.random.PCG64(1))
+    vm = 1 + 0.02 * rng.standard_normal(net.n_bus)
+    va = 0.05 * rng.standard_normal(net.n_bus)
+    va[0] = 0
+    dx = wls.multi_area_step(net, part, z[0], w, vm, va)
+    G, g = wls.gain_and_gradient(net, z[0], w, vm, va)
+    ref = np.linalg.solve(G, g)
+    assert np.max(np.abs(dx - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_area_blocks_sum_to_global_gain():
+    """sum_k E_k^T G_k E_k (lifted to the global unknowns) equals G entrywise,
+    and every unknown is internal to exactly one area or on the boundary."""
+    grid = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(grid, 1, 2500)
+    w = wls.weights(sig)
+    part = wls.partition(net, grid.area_of_bus, grid.n_area)
+    vm, va = Vm[0] * 1.01, Va[0] * 0.9
+    G, g = wls.gain_and_gradient(net, z[0], w, vm, va)
+    H = wls.jacobian(net, vm, va)
+    r = z[0] - wls.measure(net, vm, va)
+    acc = np.zeros_like(G)
+    accg = np.zeros_like(g)
+    seen = np.zeros(G.shape[0], dtype=int)
+    for k in range(grid.n_area):
+        blk = wls.area_blocks(H, w, r, part, k)
+        ic, bc = part.internal_cols[k], part.boundary_cols[k]
+        acc[np.ix_(ic, ic)] += blk.Gii
+        acc[np.ix_(ic, bc)] += blk.Gib
+        acc[np.ix_(bc, ic)] += blk.Gib.T
+        acc[np.ix_(bc, bc)] += blk.Gbb
+        np.add.at(accg, ic, blk.bi)
+        np.add.at(accg, bc, blk.bb)
+        seen[ic] += 1
+        # rows of area k touch only its local unknowns
+        Hk = H[part.rows[k]].toarray()
+        other = np.setdiff1d(np.arange(G.shape[0]), np.concatenate([ic, bc]))
+        assert np.all(Hk[:, other] == 0)
+    seen[part.gamma_cols] += 1
+    assert np.all(seen == 1)
+    np.testing.assert_allclose(acc, G, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(accg, g, rtol=1e-12, atol=1e-9)
+    assert sorted(np.concatenate(part.rows).tolist()) == list(range(net.n_meas))
+
+
+def test_multi_area_iterates_equal_centralised():
+    """Each condensed step equals the centralised GN step, so the iterates,
+    iteration counts and fixed point agree (Sec. 3; Sec. 5.3)."""
+    grid = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(grid, 1, 2600)
+    w = wls.weights(sig)
+    part = wls.partition(net, grid.area_of_bus, grid.n_area)
+    a = wls.gauss_newton(net, z[0], w, tol=1e-10, max_iter=20, keep_steps=True)
+    b = wls.multi_area_gauss_newton(net, part, z[0], w, tol=1e-10, max_iter=20, keep_steps=True)
+    assert a.converged and b.converged and a.iters == b.iters
+    for sa, sb in zip(a.steps, b.steps):
+        assert np.max(np.abs(sa - sb)) < 1e-9
+    assert np.max(np.abs(a.Vm - b.Vm)) < 1e-9
+    assert np.max(np.abs(a.Va - b.Va)) < 1e-9
+    assert abs(a.J - b.J) <= 1e-9 * a.J
+
+
+def test_masked_rows_equal_deleted_rows():
+    """Row masking (w = 0) gives the estimate of the problem with those rows
+    removed (Sec. 4.1): compared with a solve on a row-deleted system built
+    with library least squares over the complex model."""
+    grid = tiny_grid(9, 3, seed=11)
+    net, Vm, Va, z, sig = problem(grid, 1, 2700)
+    mask = synth.family_mask(grid, "Qt")[0]
+    w = wls.weights(sig, mask)
+    res = wls.gauss_newton(net, z[0], w, tol=1e-13, max_iter=30)
+    N = net.n_bus
+    keep = mask != 0
+
+    def resid(xv):
+        vm = xv[:N]
+        va = np.concatenate([[0.0], xv[N:]])
+        Sf, St = _complex_flows(net, vm, va)
+        Si = _ybus_injection(net, vm, va)
+        h = np.concatenate([vm, Si.real, Si.imag, Sf.real, Sf.imag, St.real, St.imag])
+        return (z[0] - h)[keep] / sig[keep]
+
+    ls = so.least_squares(resid, np.concatenate([np.ones(N), np.zeros(N - 1)]),
+                          xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    np.testing.assert_allclose(res.Vm, ls.x[:N], atol=1e-8)
+    np.testing.assert_allclose(res.Va[1:], ls.x[N:], atol=1e-8)
+
+
+def test_objective_follows_chi_square_law():
+    """At the WLS estimate, r^T W r ~ chi^2 with m - n degrees of freedom
+    (the relation visible in the printed objectives, Sec. 5.3)."""
+    grid = synth.make_grid("grid300_k4")
+    vals = []
+    for seed in range(3):
+        net, Vm, Va, z, sig = problem(grid, 1, 2800 + 10 * seed)
+        w = wls.weights(sig)
+        vals.append(wls.gauss_newton(net, z[0], w, tol=1e-10).J)
+    dof = net.n_meas - (2 * net.n_bus - 1)
+    for J in vals:
+        assert abs(J - dof) < 4 * np.sqrt(2 * dof)
