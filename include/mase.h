@@ -1,0 +1,201 @@
+/*
+ * mase.h - C ABI of libmase: GB300-native multi-area weighted-least-squares
+ * (WLS) power-system state estimation by boundary-condensed Gauss-Newton.
+ *
+ * Method (arXiv 2604.23175):
+ *   - measurement model z = h(x) + e, WLS objective J = r^T W r,
+ *     r = z - h(x), W = R^{-1}                      (Sec. 2.1, Eqs. meas_model, wls)
+ *   - Gauss-Newton step G dx = H^T W r, G = H^T W H   (Sec. 2.1, Eq. gn_normal)
+ *   - typed measurement templates evaluated without forming H
+ *                                                    (Sec. 2.2, Eq. typed_meas; Sec. 4.1-4.2)
+ *   - per-area blocks, Schur condensation S_b = G_bb - G_bi G_ii^{-1} G_ib,
+ *     b_hat = b_b - G_bi G_ii^{-1} b_i              (Sec. 3.1-3.2, Eqs. block_normal, schur_defs)
+ *   - coordinator S_Gamma = sum_k E_k^T S_b^k E_k, solve, scatter back,
+ *     interior recovery                              (Sec. 3.2, Eqs. global_assembly, backsub;
+ *                                                     Sec. 4.3-4.4)
+ *
+ * Conventions used by every entry point:
+ *   - Bus indices are 0-based int32.  Angles are radians, per unit elsewhere.
+ *   - State layout x[n_snap][2*n_bus] = (Vm[0..N), Va[0..N)) per snapshot.
+ *     The slack angle is held at its value in x0 (0 for a flat start), so a
+ *     snapshot has n = 2N - 1 unknowns.
+ *   - Canonical measurement row order, m = 3N + 4L:
+ *       Vm[N], Pinj[N], Qinj[N], Pf[L], Qf[L], Pt[L], Qt[L]
+ *     "f" rows are measured at the from end of a branch, "t" rows at its to
+ *     end; injections are positive into the network.
+ *   - Branch model: pi equivalent, series admittance 1/(r + jx), total line
+ *     charging b split b/2 at each end; no taps, no bus shunts.
+ *   - Pointers to per-snapshot arrays (z, mask, x0, x_out) may point to host
+ *     or device memory; the library asks the CUDA runtime which.  All other
+ *     pointers are host pointers.  The caller keeps ownership of everything
+ *     it passes; the library copies what it needs before returning.
+ *   - Return value: MASE_OK (0), a negative error code, or MASE_NOT_CONVERGED
+ *     (positive) from mase_solve.  mase_status_str() names each code and
+ *     mase_last_error() gives the message of the last failure on this thread.
+ *   - A handle is not re-entrant: do not call it from two threads at once.
+ *     Distinct handles are independent.  Work is enqueued on the stream given
+ *     in mase_options (NULL = the legacy default stream); calls return after
+ *     their results are available to the caller.
+ */
+#ifndef MASE_H
+#define MASE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MASE_OK                 0
+#define MASE_NOT_CONVERGED      1   /* some snapshot reached max_iter         */
+#define MASE_EINVAL           (-1)  /* bad size, index, pointer or option     */
+#define MASE_EUNOBSERVABLE    (-2)  /* non-positive pivot: G_ii or S_Gamma not SPD */
+#define MASE_ENONFINITE       (-3)  /* NaN/Inf in inputs or iterates          */
+#define MASE_EDEVICE          (-4)  /* CUDA error, out of device memory        */
+#define MASE_ENOTREADY        (-5)  /* no measurements / no warm-start model  */
+
+/* per-snapshot status codes written to mase_stats.status */
+#define MASE_SNAP_CONVERGED     0
+#define MASE_SNAP_MAX_ITER      1
+#define MASE_SNAP_NOT_SPD       2
+#define MASE_SNAP_NONFINITE     3
+
+/* precision modes */
+#define MASE_FP64   0   /* every step in FP64 (the plain comparator)               */
+#define MASE_MIXED  1   /* FP32 gain, factor, Schur and local solves; FP64 residual,
+                           gradient H^T W r, boundary refinement and update        */
+/* start modes */
+#define MASE_START_FLAT     0   /* Vm = 1, Va = 0                               */
+#define MASE_START_X0       1   /* x0 given to mase_solve                        */
+#define MASE_START_LEARNED  2   /* per-area MLP proposal (mase_warmstart_*),
+                                   kept only where it lowers J below the flat start */
+/* schedule modes */
+#define MASE_PER_AREA   0   /* one launch per area and stage, like per-area streams */
+#define MASE_BATCHED    1   /* one launch per stage over every (area, snapshot)   */
+
+typedef struct mase_handle mase_handle;
+
+/* Network (Sec. 2.1 bus-branch model).  Arrays have n_branch entries. */
+typedef struct {
+    int32_t n_bus, n_branch, slack_bus;
+    const int32_t *from_bus, *to_bus;   /* 0-based, from != to                    */
+    const double *r, *x;                /* series resistance, reactance (p.u.)    */
+    const double *b_charge;             /* total line charging (p.u.)             */
+} mase_network;
+
+/* Partition into K areas (Sec. 2.3).  area_of_bus[n_bus] in [0, n_area);
+ * every area must own at least one bus. */
+typedef struct {
+    int32_t n_area;
+    const int32_t *area_of_bus;
+} mase_partition;
+
+/* Measurements (Sec. 2.1, 4.1).  sigma[m] is shared by all snapshots
+ * (W = diag(1/sigma^2)); mask[n_snap][m] (1 = present, 0 = masked, weight 0)
+ * or NULL for all present; z[n_snap][m] or NULL to supply it later with
+ * mase_set_measurements. */
+typedef struct {
+    int32_t n_snap;
+    const double *z;
+    const double *sigma;
+    const uint8_t *mask;
+} mase_measurements;
+
+typedef struct {
+    int32_t precision;   /* MASE_FP64 | MASE_MIXED                     */
+    int32_t schedule;    /* MASE_PER_AREA | MASE_BATCHED               */
+    int32_t use_graph;   /* 1: replay each iteration as a CUDA graph    */
+    int32_t refine;      /* boundary refinement sweeps (MIXED), e.g. 1  */
+    int32_t threads;     /* threads per CTA of the area kernels, 0=auto */
+    int32_t device;      /* CUDA device ordinal                         */
+    void   *stream;      /* cudaStream_t, NULL = default stream         */
+} mase_options;
+
+/* Per-solve results.  Arrays are host arrays of n_snap entries supplied by
+ * the caller (any may be NULL). */
+typedef struct {
+    int32_t *iters;       /* Gauss-Newton steps taken per snapshot              */
+    int32_t *status;      /* MASE_SNAP_* per snapshot                           */
+    double  *J;           /* r^T W r at the returned state, per snapshot        */
+    double  *max_step;    /* max |dx| of the last step, per snapshot            */
+    double   stage_ms[4]; /* device time: local / boundary / back-substitution /
+                             other, summed over the solve (0 unless profiling)  */
+    int32_t  total_launches; /* kernels launched by the solve                   */
+} mase_stats;
+
+/* Structural sizes of a handle (host-side setup results). */
+typedef struct {
+    int32_t n_bus, n_branch, n_area, n_snap, n_meas, n_state;
+    int32_t n_boundary_bus, n_gamma;        /* |boundary buses|, dim x_Gamma   */
+    int32_t max_area_vars, max_area_nb;     /* largest n_i + n_b, largest n_b   */
+    int64_t factor_nnz;                     /* sum over areas of stored factor entries */
+    int64_t local_flops, boundary_flops;    /* per snapshot and GN step (multiply-adds) */
+    int64_t g_updates;                      /* gain-matrix scalar updates per snapshot */
+    int32_t smem_bytes_max;                 /* largest per-area shared-memory need */
+    int32_t areas_in_smem;                  /* areas whose factor fits shared memory */
+} mase_info;
+
+/* Default options: MIXED, BATCHED, graph on, 1 refinement sweep, device 0. */
+void mase_default_options(mase_options *opt);
+
+/* Build a handle: validates the inputs, runs the one-time symbolic setup
+ * (boundary sets and selectors E_k, measurement templates and gain-matrix
+ * slot maps, fill-reducing orderings and supernodal symbolic factors of every
+ * area and of the boundary system; Sec. 4.1, 4.3) and allocates every device
+ * buffer once (Sec. 5.1).  meas->n_snap fixes the batch size.
+ * Errors: MASE_EINVAL (sizes, indices, from == to, sigma <= 0, empty area),
+ * MASE_EDEVICE.  *out is set only on success. */
+int mase_create(const mase_network *net, const mase_partition *part,
+                const mase_measurements *meas, const mase_options *opt,
+                mase_handle **out);
+
+/* Replace z (and the mask if meas->mask != NULL) for the next solve.
+ * meas->n_snap must equal the handle's batch size; sigma is ignored. */
+int mase_set_measurements(mase_handle *h, const mase_measurements *meas);
+
+/* Solve every snapshot of the batch by Gauss-Newton from the start given by
+ * the handle's start mode: x0 (n_snap x 2N) is used when non-NULL, otherwise
+ * a flat start (or the learned start after mase_set_start_mode).  Stops a
+ * snapshot once max|dx| < tol (the step is applied) or after max_iter steps.
+ * x_out (n_snap x 2N) receives the estimates.  Returns MASE_OK,
+ * MASE_NOT_CONVERGED, or an error; per-snapshot details go to stats. */
+int mase_solve(mase_handle *h, const double *x0, double tol, int32_t max_iter,
+               double *x_out, mase_stats *stats);
+
+/* Evaluate h(x) for n_snap states x[n_snap][2N] into z_out[n_snap][m]
+ * (canonical order).  Uses the handle's network; x and z_out host or device. */
+int mase_measure(mase_handle *h, const double *x, int32_t n_snap, double *z_out);
+
+/* Structural information filled by mase_create. */
+int mase_get_info(const mase_handle *h, mase_info *info);
+
+/* Choose the start mode used by mase_solve when x0 is NULL. */
+int mase_set_start_mode(mase_handle *h, int32_t start_mode);
+
+/* Host-only: run the one-time symbolic setup of mase_create (Sec. 4.1, 4.3)
+ * without touching a GPU and report its structural sizes (n_snap and
+ * smem fields are left 0).  Errors: MASE_EINVAL (see mase_analyze_error). */
+int mase_analyze(const mase_network *net, const mase_partition *part, mase_info *info);
+
+/* Host-only consistency check of the symbolic setup: random gain terms are
+ * scattered through the slot maps as the device accumulation does and the
+ * supernodal schedule is run serially in FP64.  errors4 receives the maximum
+ * relative errors {slot maps vs dense assembly, Schur blocks vs dense Schur
+ * complements (Eq. schur_defs), area solves vs dense solves, boundary solve
+ * vs dense solve}.  Returns MASE_EINVAL on a structural inconsistency. */
+int mase_selfcheck(const mase_network *net, const mase_partition *part, uint64_t seed,
+                   double *errors4);
+
+/* Message of the last mase_analyze / mase_selfcheck failure on this thread. */
+const char *mase_analyze_error(void);
+
+void mase_destroy(mase_handle *h);
+const char *mase_status_str(int code);
+const char *mase_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MASE_H */

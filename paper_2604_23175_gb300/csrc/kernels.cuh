@@ -1,0 +1,861 @@
+// Device code of libmase (sm_103a).
+//
+// One thread block works on one (area, snapshot) instance.  The whole local
+// pipeline of an iteration (Sec. 4.1-4.3) runs inside it: typed measurement
+// templates are evaluated (Eq. typed_meas), the residual, the gradient
+// H^T W r (FP64) and the gain matrix G = H^T W H are accumulated straight
+// into the area's supernodal factor storage without forming H (Sec. 4.2),
+// and the supernodal Cholesky of G_ii with the boundary block ordered last
+// leaves the Schur complement S_b and the condensed right-hand side in place
+// (Eq. schur_defs, "Schur mode", Sec. 4.3).  The coordinator assembles and
+// factors the sparse boundary system per snapshot (Eq. global_assembly,
+// Sec. 4.4) and the back-substitution kernel recovers the interior step
+// (Eq. backsub).
+//
+// Precision: RG is the gain/factor/Schur type, RS the type of the local
+// triangular solves.  Residuals, the gradient, the boundary refinement and the
+// state update are always FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mase_dev {
+
+constexpr int WIDE = 24;   // supernodes wider than this are factored by the whole block
+
+// Symbolic factor descriptor (all indices relative to its bases).
+struct FacDev {
+    int n_int, n_bnd, nsn, nlev;
+    int store_int, store_total, off_B, max_w;
+    int sn_base;       // per-supernode arrays
+    int lev_base;      // lev_items
+    int levoff_base;   // lev_off (nlev + 1 entries)
+    int rows_base;     // rows / colbase / relbase
+    int rel_base;      // rel
+};
+
+struct AreaDev {
+    FacDev F;
+    int nb_int, nb_loc, n_own, n_ends, n_slots, n_items;
+    int bus_base, own_base, own1_base, end_base, slot_base, item_base, ebnd_base;
+    int zrow_base;
+    int in_smem;
+    int off_g, off_y, off_bus, off_end, off_inj, off_self, off_st;   // dynamic smem byte offsets
+    int smem_bytes;
+    long long fac_base;     // element offset of (area, snapshot 0) in the factor buffer
+    int fac_stride;         // elements per snapshot (= store_total)
+    long long c_base;       // interior forward-solved rhs, stride n_int
+    long long bh_base;      // condensed boundary rhs, stride n_bnd
+};
+
+struct Tables {
+    const int *sn_c0, *sn_w, *sn_nr, *sn_off, *sn_rows, *sn_order, *item_off;
+    const int *lev_items, *lev_off;
+    const int *rows, *colbase, *relbase, *rel;
+    const int *locbus, *qvarV, *qvarT;
+    const int *own_q, *own_gvv, *own_ebeg, *own_sbeg;
+    const int *end_qi, *end_qj, *end_own, *end_var, *end_gpos;
+    const double *end_g, *end_b, *end_bh;
+    const int *slot_q, *slot_ebeg, *slot_ecnt;
+    const int *item_own, *item_uv, *item_pos;
+    const int *ebnd;
+};
+
+struct State {
+    int N, M, S;                 // buses, measurement rows, snapshots
+    double *xV, *xT;             // [S][N] internal bus numbering
+    const double *z;             // [S][M] internal row order
+    const double *W;             // [M] 1/sigma^2
+    const uint8_t *mask;         // [S][M] or null
+    int *active;                 // [S]
+    int *err;                    // [S] bit 1: non-SPD pivot, bit 2: non-finite
+    double *J;                   // [S]
+    unsigned long long *maxstep; // [S] bit pattern of max |dx| (non-negative double)
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += red[i];
+    return t;   // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+    return t;
+}
+
+// P and Q leaving bus i into a branch towards j (pi model, Sec. 2.1 bus-branch
+// formulation), from cos/sin of both angles: theta_ij = theta_i - theta_j.
+struct EndFlow {
+    double P, Q, gc_bs, gs_bc;
+};
+__device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, double si, double cj,
+                                            double sj, double g, double b, double bh) {
+    const double c = ci * cj + si * sj;      // cos(theta_i - theta_j)
+    const double s = si * cj - ci * sj;      // sin(theta_i - theta_j)
+    EndFlow f;
+    f.gc_bs = g * c + b * s;
+    f.gs_bc = g * s - b * c;
+    const double ViVj = Vi * Vj;
+    f.P = Vi * Vi * g - ViVj * f.gc_bs;
+    f.Q = -Vi * Vi * (b + bh) - ViVj * f.gs_bc;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// supernodal factorisation with trailing Schur block + forward solve
+// ---------------------------------------------------------------------------
+
+// Right-looking column Cholesky of one supernode panel by one warp
+// (diagonal block + rows below), fused with the forward solve of its rhs.
+template <class RG, class RS>
+__device__ void panel_warp(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
+    for (int c = 0; c < w; ++c) {
+        RG *col = P + (size_t)c * ld;
+        if (do_factor) {
+            RG d = col[c];
+            if (!(d > RG(0))) {
+                if (lane == 0) *err = 1;
+                d = RG(1);
+            }
+            const RG sd = sqrt(d);
+            const RG inv = RG(1) / sd;
+            __syncwarp();
+            for (int r = c + 1 + lane; r < ld; r += 32) col[r] *= inv;
+            if (lane == 0) col[c] = sd;
+            __syncwarp();
+            for (int c2 = c + 1; c2 < w; ++c2) {
+                const RG l = col[c2];
+                RG *col2 = P + (size_t)c2 * ld;
+                for (int r = c2 + lane; r < ld; r += 32) col2[r] -= col[r] * l;
+            }
+            __syncwarp();
+        }
+        const RS yv = yc[c] / RS(col[c]);
+        __syncwarp();
+        if (lane == 0) yc[c] = yv;
+        for (int r = c + 1 + lane; r < w; r += 32) yc[r] -= RS(col[r]) * yv;
+        __syncwarp();
+    }
+}
+
+// Same panel, by the whole block (wide supernodes near the elimination-tree root).
+template <class RG, class RS>
+__device__ void panel_block(RG *P, int w, int ld, RS *yc, bool do_factor, int *err) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (do_factor) {
+        for (int c = 0; c < w; ++c) {
+            RG *col = P + (size_t)c * ld;
+            __syncthreads();
+            RG d = col[c];
+            if (!(d > RG(0))) {
+                if (tid == 0) *err = 1;
+                d = RG(1);
+            }
+            const RG sd = sqrt(d);
+            const RG inv = RG(1) / sd;
+            __syncthreads();
+            for (int r = c + 1 + tid; r < ld; r += nt) col[r] *= inv;
+            if (tid == 0) col[c] = sd;
+            __syncthreads();
+            const int ncol = w - c - 1;
+            for (int idx = tid; idx < ncol * ld; idx += nt) {
+                const int c2 = c + 1 + idx / ld, r = idx % ld;
+                if (r >= c2) P[(size_t)c2 * ld + r] -= col[r] * col[c2];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {
+        for (int c = 0; c < w; ++c) {
+            const RG *col = P + (size_t)c * ld;
+            const RS yv = yc[c] / RS(col[c]);
+            __syncwarp();
+            if (tid == 0) yc[c] = yv;
+            for (int r = c + 1 + tid; r < w; r += 32) yc[r] -= RS(col[r]) * yv;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// Factor (optionally) and forward-solve the internal supernodes level by
+// level.  Updates of ancestors -- including the trailing Schur block and the
+// boundary part of the rhs -- are scattered with atomics through the
+// relative-index maps.  Must be called by every thread of the block.
+template <class RG, class RS>
+__device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, bool do_factor,
+                               int *err) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
+    const int *sn_order = T.sn_order + F.sn_base;
+    const int *item_off = T.item_off + F.sn_base;
+    const int *lev_off = T.lev_off + F.levoff_base;
+    for (int lev = 0; lev < F.nlev; ++lev) {
+        const int a = lev_off[lev], e = lev_off[lev + 1];
+        for (int i = a + warp; i < e; i += nw) {
+            const int s = F.sn_base + sn_order[i];
+            const int w = T.sn_w[s];
+            if (w > WIDE) continue;
+            panel_warp<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
+                               lane, err);
+        }
+        for (int i = a; i < e; ++i) {
+            const int s = F.sn_base + sn_order[i];
+            const int w = T.sn_w[s];
+            if (w <= WIDE) continue;
+            panel_block<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
+                                err);
+        }
+        __syncthreads();
+        if (do_factor) {
+            const int nit = T.lev_items[F.lev_base + lev];
+            for (int it = tid; it < nit; it += nt) {
+                int lo = a, hi = e - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (item_off[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int s = F.sn_base + sn_order[lo];
+                const int loc = it - item_off[lo];
+                const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
+                const RG *Ps = st + T.sn_off[s] + w;
+                const int rb = F.rows_base + T.sn_rows[s];
+                const int P2 = R * (R + 1) / 2;
+                if (loc < P2) {
+                    int ir = (int)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
+                    while (ir * (ir + 1) / 2 > loc) --ir;
+                    while ((ir + 1) * (ir + 2) / 2 <= loc) ++ir;
+                    const int jr = loc - ir * (ir + 1) / 2;
+                    RG v = RG(0);
+                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
+                    const int tgt = T.colbase[rb + jr] + T.rel[F.rel_base + T.relbase[rb + jr] + ir];
+                    atomicAdd(st + tgt, -v);
+                } else {
+                    const int ir = loc - P2;
+                    const RS *yc = y + T.sn_c0[s];
+                    RS v = RS(0);
+                    for (int c = 0; c < w; ++c) v += RS(Ps[(size_t)c * ld + ir]) * yc[c];
+                    atomicAdd(y + T.rows[rb + ir], -v);
+                }
+            }
+        } else {
+            for (int i = a + warp; i < e; i += nw) {
+                const int s = F.sn_base + sn_order[i];
+                const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
+                const RG *Ps = st + T.sn_off[s] + w;
+                const int rb = F.rows_base + T.sn_rows[s];
+                const RS *yc = y + T.sn_c0[s];
+                for (int ir = lane; ir < R; ir += 32) {
+                    RS v = RS(0);
+                    for (int c = 0; c < w; ++c) v += RS(Ps[(size_t)c * ld + ir]) * yc[c];
+                    atomicAdd(y + T.rows[rb + ir], -v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Backward solve L^T x = y over the internal supernodes, top level first.
+// y[n_int..] must hold the (already known) boundary unknowns; on return
+// y[0..n_int) holds the interior solution (Eq. backsub).
+template <class RG, class RS>
+__device__ void back_solve(const FacDev &F, const Tables &T, const RG *st, RS *y) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int *sn_order = T.sn_order + F.sn_base;
+    const int *lev_off = T.lev_off + F.levoff_base;
+    for (int lev = F.nlev - 1; lev >= 0; --lev) {
+        const int a = lev_off[lev], e = lev_off[lev + 1];
+        for (int i = a + warp; i < e; i += nw) {
+            const int s = F.sn_base + sn_order[i];
+            const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R, c0 = T.sn_c0[s];
+            const RG *P = st + T.sn_off[s];
+            const int *rows = T.rows + F.rows_base + T.sn_rows[s];
+            for (int c = 0; c < w; ++c) {
+                RS acc = RS(0);
+                for (int i2 = lane; i2 < R; i2 += 32) acc += RS(P[(size_t)c * ld + w + i2]) * y[rows[i2]];
+                acc = warp_sum(acc);
+                if (lane == 0) y[c0 + c] -= acc;
+            }
+            __syncwarp();
+            for (int c = w - 1; c >= 0; --c) {
+                RS acc = RS(0);
+                for (int r = c + 1 + lane; r < w; r += 32) acc += RS(P[(size_t)c * ld + r]) * y[c0 + r];
+                acc = warp_sum(acc);
+                if (lane == 0) y[c0 + c] = (y[c0 + c] - acc) / RS(P[(size_t)c * ld + c]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// local kernel: evaluation + fused accumulation + Schur condensation
+// ---------------------------------------------------------------------------
+enum { MODE_FULL = 0, MODE_OBJECTIVE = 1 };
+
+template <class RG, class RS>
+__global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas, Tables T, State X,
+                                               const int2 *__restrict__ inst, int area_only,
+                                               int mode, RG *fac, RS *cvec, double *bh) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_err;
+    int k, s;
+    if (area_only >= 0) {
+        k = area_only;
+        s = blockIdx.x;
+    } else {
+        const int2 ks = inst[blockIdx.x];
+        k = ks.x;
+        s = ks.y;
+    }
+    if (mode == MODE_FULL && !X.active[s]) return;
+    const AreaDev A = areas[k];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nv = A.F.n_int + A.F.n_bnd;
+    double *g = (double *)(smem + A.off_g);
+    RS *y = (RS *)(smem + A.off_y);
+    double *bV = (double *)(smem + A.off_bus);
+    double *bT = bV + A.nb_loc;
+    double *bC = bT + A.nb_loc;
+    double *bS = bC + A.nb_loc;
+    unsigned char *endbuf = smem + A.off_end;
+    double2 *inj = (double2 *)(smem + A.off_inj);
+    RG *self = (RG *)(smem + A.off_self);
+    RG *st = A.in_smem ? (RG *)(smem + A.off_st) : fac + A.fac_base + (long long)s * A.fac_stride;
+    const int endstride = (4 * sizeof(RG) > 16) ? 4 * (int)sizeof(RG) : 16;
+
+    const long long zb = (long long)s * X.M + A.zrow_base;
+    const double *z = X.z + zb;
+    const double *Wr = X.W + A.zrow_base;
+    const uint8_t *mk = X.mask ? X.mask + zb : nullptr;
+    auto wt = [&](int r) { return mk ? (mk[r] ? Wr[r] : 0.0) : Wr[r]; };
+    const int n_own = A.n_own, n_ends = A.n_ends;
+    const int rV = 0, rP = n_own, rQ = 2 * n_own, rPe = 3 * n_own, rQe = 3 * n_own + n_ends;
+
+    if (tid == 0) s_err = 0;
+    // ---- E0: bus values, zero accumulators
+    for (int q = tid; q < A.nb_loc; q += nt) {
+        const int ib = T.locbus[A.bus_base + q];
+        const double V = X.xV[(long long)s * X.N + ib], th = X.xT[(long long)s * X.N + ib];
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        bV[q] = V;
+        bT[q] = th;
+        bC[q] = cs;
+        bS[q] = sn;
+    }
+    if (mode == MODE_FULL) {
+        for (int i = tid; i < nv; i += nt) g[i] = 0.0;
+        for (int i = tid; i < A.F.store_total; i += nt) st[i] = RG(0);
+        for (int i = tid; i < 4 * n_own; i += nt) self[i] = RG(0);
+    }
+    __syncthreads();
+    // ---- E1: flows at every owned branch end (FP64)
+    for (int e = tid; e < n_ends; e += nt) {
+        const int ee = A.end_base + e;
+        const int qi = T.end_qi[ee], qj = T.end_qj[ee];
+        const EndFlow f = end_flow(bV[qi], bV[qj], bC[qi], bS[qi], bC[qj], bS[qj], T.end_g[ee],
+                                   T.end_b[ee], T.end_bh[ee]);
+        double2 *pq = (double2 *)(endbuf + (size_t)e * endstride);
+        *pq = make_double2(f.P, f.Q);
+    }
+    __syncthreads();
+    // ---- E2: voltage rows and injection residuals per own bus
+    double Jloc = 0.0;
+    for (int o = tid; o < n_own; o += nt) {
+        const int q = T.own_q[A.own_base + o];
+        const double V = bV[q];
+        const double wv = wt(rV + o), rv = z[rV + o] - V;
+        Jloc += wv * rv * rv;
+        double Pi = 0.0, Qi = 0.0;
+        const int e0 = T.own_ebeg[A.own1_base + o], e1 = T.own_ebeg[A.own1_base + o + 1];
+        for (int e = e0; e < e1; ++e) {
+            const double2 pq = *(const double2 *)(endbuf + (size_t)e * endstride);
+            Pi += pq.x;
+            Qi += pq.y;
+        }
+        const double wp = wt(rP + o), wq = wt(rQ + o);
+        const double rp = z[rP + o] - Pi, rq = z[rQ + o] - Qi;
+        Jloc += wp * rp * rp + wq * rq * rq;
+        inj[o] = make_double2(wp * rp, wq * rq);
+        if (mode == MODE_FULL) {
+            atomicAdd(g + T.qvarV[A.bus_base + q], wv * rv);
+            atomicAdd(st + T.own_gvv[A.own_base + o], RG(wv));
+        }
+    }
+    __syncthreads();
+    // ---- E3: flow rows; gradient of flow and injection rows; flow-row gain terms
+    for (int e = tid; e < n_ends; e += nt) {
+        const int ee = A.end_base + e;
+        const int qi = T.end_qi[ee], qj = T.end_qj[ee];
+        const double2 pq = *(const double2 *)(endbuf + (size_t)e * endstride);
+        const double wPe = wt(rPe + e), wQe = wt(rQe + e);
+        const double rPf = z[rPe + e] - pq.x, rQf = z[rQe + e] - pq.y;
+        Jloc += wPe * rPf * rPf + wQe * rQf * rQf;
+        if (mode != MODE_FULL) continue;
+        const double Vi = bV[qi], Vj = bV[qj];
+        const double g_ = T.end_g[ee], b_ = T.end_b[ee], bh_ = T.end_bh[ee];
+        const EndFlow f = end_flow(Vi, Vj, bC[qi], bS[qi], bC[qj], bS[qj], g_, b_, bh_);
+        const double ViVj = Vi * Vj;
+        // partials w.r.t. (Vi, thi, Vj, thj)
+        double dP[4], dQ[4];
+        dP[0] = 2.0 * Vi * g_ - Vj * f.gc_bs;
+        dP[1] = ViVj * f.gs_bc;
+        dP[2] = -Vi * f.gc_bs;
+        dP[3] = -dP[1];
+        dQ[0] = -2.0 * Vi * (b_ + bh_) - Vj * f.gs_bc;
+        dQ[1] = -ViVj * f.gc_bs;
+        dQ[2] = -Vi * f.gs_bc;
+        dQ[3] = -dQ[1];
+        const int o = T.end_own[ee];
+        const double2 ij = inj[o];
+        const double aP = wPe * rPf + ij.x, aQ = wQe * rQf + ij.y;
+        const int *vv = T.end_var + 4 * (long long)ee;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int v = vv[a];
+            if (v >= 0) atomicAdd(g + v, aP * dP[a] + aQ * dQ[a]);
+        }
+        RG hP[4], hQ[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            hP[a] = RG(dP[a]);
+            hQ[a] = RG(dQ[a]);
+        }
+        const RG wp = RG(wPe), wq = RG(wQe);
+        const int *gp = T.end_gpos + 10 * (long long)ee;
+        int idx = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = a; c < 4; ++c, ++idx) {
+                const int p = gp[idx];
+                if (p >= 0) atomicAdd(st + p, wp * hP[a] * hP[c] + wq * hQ[a] * hQ[c]);
+            }
+        // injection partials: own-bus part summed per bus, neighbour part kept per end
+        atomicAdd(self + 4 * o + 0, hP[0]);
+        atomicAdd(self + 4 * o + 1, hP[1]);
+        atomicAdd(self + 4 * o + 2, hQ[0]);
+        atomicAdd(self + 4 * o + 3, hQ[1]);
+        RG *nb = (RG *)(endbuf + (size_t)e * endstride);
+        nb[0] = hP[2];
+        nb[1] = hP[3];
+        nb[2] = hQ[2];
+        nb[3] = hQ[3];
+    }
+    if (mode != MODE_FULL) {
+        const double Js = block_sum(Jloc, red);
+        if (tid == 0) atomicAdd(X.J + s, Js);
+        return;
+    }
+    __syncthreads();
+    // ---- E4: injection-row gain terms, one item per pair of buses in the row
+    for (int it = tid; it < A.n_items; it += nt) {
+        const int ii = A.item_base + it;
+        const int o = T.item_own[ii];
+        const int uv = T.item_uv[ii];
+        const int u = uv & 0xffff, v = uv >> 16;
+        const int sb = T.own_sbeg[A.own1_base + o];
+        RG pu[4], pv[4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int sl = t == 0 ? u : v;
+            RG *dst = t == 0 ? pu : pv;
+            if (sl == 0) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) dst[a] = self[4 * o + a];
+            } else {
+                const int ss = A.slot_base + sb + sl - 1;
+                const int eb = T.slot_ebeg[ss], ec = T.slot_ecnt[ss];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) dst[a] = RG(0);
+                for (int e = eb; e < eb + ec; ++e) {
+                    const RG *nb = (const RG *)(endbuf + (size_t)e * endstride);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) dst[a] += nb[a];
+                }
+            }
+        }
+        // pu = (dP/dV_u, dP/dth_u, dQ/dV_u, dQ/dth_u)
+        const RG wp = RG(wt(rP + o)), wq = RG(wt(rQ + o));
+        const int *p4 = T.item_pos + 4 * (long long)ii;
+        if (u == v) {
+            atomicAdd(st + p4[0], wp * pu[0] * pu[0] + wq * pu[2] * pu[2]);
+            if (p4[1] >= 0) atomicAdd(st + p4[1], wp * pu[1] * pu[0] + wq * pu[3] * pu[2]);
+            if (p4[2] >= 0) atomicAdd(st + p4[2], wp * pu[1] * pu[1] + wq * pu[3] * pu[3]);
+        } else {
+            atomicAdd(st + p4[0], wp * pu[0] * pv[0] + wq * pu[2] * pv[2]);
+            if (p4[1] >= 0) atomicAdd(st + p4[1], wp * pu[0] * pv[1] + wq * pu[2] * pv[3]);
+            if (p4[2] >= 0) atomicAdd(st + p4[2], wp * pu[1] * pv[0] + wq * pu[3] * pv[2]);
+            if (p4[3] >= 0) atomicAdd(st + p4[3], wp * pu[1] * pv[1] + wq * pu[3] * pv[3]);
+        }
+    }
+    __syncthreads();
+    // ---- rhs in solve precision
+    for (int i = tid; i < nv; i += nt) y[i] = RS(g[i]);
+    __syncthreads();
+    // ---- Schur-mode factorisation (Sec. 4.3): leaves S_b and b_hat in the trailing block
+    factor_forward<RG, RS>(A.F, T, st, y, true, &s_err);
+    // ---- outputs
+    if (A.in_smem) {
+        RG *dst = fac + A.fac_base + (long long)s * A.fac_stride;
+        for (int i = tid; i < A.F.store_total; i += nt) dst[i] = st[i];
+    }
+    RS *cdst = cvec + A.c_base + (long long)s * A.F.n_int;
+    for (int i = tid; i < A.F.n_int; i += nt) cdst[i] = y[i];
+    double *bdst = bh + A.bh_base + (long long)s * A.F.n_bnd;
+    for (int i = tid; i < A.F.n_bnd; i += nt) bdst[i] = double(y[A.F.n_int + i]);
+    const double Js = block_sum(Jloc, red);
+    if (tid == 0) {
+        atomicAdd(X.J + s, Js);
+        if (s_err) atomicOr(X.err + s, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// coordinator: assembly (Eq. global_assembly), sparse Cholesky, FP64 refinement
+// ---------------------------------------------------------------------------
+struct BndDev {
+    FacDev F;
+    int n_gamma;
+    const int *asm_beg, *asm_area, *asm_off;
+    const int *rhs_beg, *rhs_area, *rhs_lv;
+    const int *bvar_ibus, *bvar_isT;
+    long long stride;     // storage elements per snapshot
+};
+
+template <class RG, class RS>
+__global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ areas, Tables T,
+                                                  State X, BndDev B, const RG *__restrict__ fac,
+                                                  const double *__restrict__ bh, RG *bst, RG *bA,
+                                                  double *dxG, int refine) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_err;
+    const int s = blockIdx.x;
+    if (!X.active[s]) return;
+    const int tid = threadIdx.x, nt = blockDim.x, nG = B.n_gamma;
+    double *bhat = (double *)smem;
+    double *x = bhat + nG;
+    double *r = x + nG;
+    RS *y = (RS *)(r + nG);
+    RG *st = bst + (long long)s * B.stride;
+    RG *Am = bA + (long long)s * B.stride;
+    if (tid == 0) s_err = 0;
+    for (int P = tid; P < B.F.store_total; P += nt) {
+        RG v = RG(0);
+        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i) {
+            const AreaDev &A = areas[B.asm_area[i]];
+            v += fac[A.fac_base + (long long)s * A.fac_stride + B.asm_off[i]];
+        }
+        st[P] = v;
+        Am[P] = v;
+    }
+    for (int gi = tid; gi < nG; gi += nt) {
+        double v = 0.0;
+        for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i) {
+            const AreaDev &A = areas[B.rhs_area[i]];
+            v += bh[A.bh_base + (long long)s * A.F.n_bnd + B.rhs_lv[i]];
+        }
+        bhat[gi] = v;
+        y[gi] = RS(v);
+    }
+    __syncthreads();
+    factor_forward<RG, RS>(B.F, T, st, y, true, &s_err);
+    back_solve<RG, RS>(B.F, T, st, y);
+    for (int gi = tid; gi < nG; gi += nt) x[gi] = double(y[gi]);
+    __syncthreads();
+    for (int it = 0; it < refine; ++it) {
+        // r = b_hat - S_Gamma x, FP64 accumulation over the stored lower triangle
+        for (int gi = tid; gi < nG; gi += nt) r[gi] = bhat[gi];
+        __syncthreads();
+        const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+        for (int sn = warp; sn < B.F.nsn; sn += nw) {
+            const int sg = B.F.sn_base + sn;
+            const int w = T.sn_w[sg], R = T.sn_nr[sg], ld = w + R, c0 = T.sn_c0[sg];
+            const RG *P = Am + T.sn_off[sg];
+            const int *rows = T.rows + B.F.rows_base + T.sn_rows[sg];
+            for (int c = 0; c < w; ++c) {
+                const int col = c0 + c;
+                double accc = 0.0;
+                for (int rr = c + lane; rr < ld; rr += 32) {
+                    const int row = rr < w ? c0 + rr : rows[rr - w];
+                    const double a = double(P[(size_t)c * ld + rr]);
+                    if (row == col) {
+                        accc += a * x[col];
+                    } else {
+                        atomicAdd(r + row, -a * x[col]);
+                        accc += a * x[row];
+                    }
+                }
+                accc = warp_sum(accc);
+                if (lane == 0) atomicAdd(r + col, -accc);
+            }
+        }
+        __syncthreads();
+        for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
+        __syncthreads();
+        factor_forward<RG, RS>(B.F, T, st, y, false, &s_err);
+        back_solve<RG, RS>(B.F, T, st, y);
+        for (int gi = tid; gi < nG; gi += nt) x[gi] += double(y[gi]);
+        __syncthreads();
+    }
+    double mx = 0.0;
+    bool bad = false;
+    for (int gi = tid; gi < nG; gi += nt) {
+        const double d = x[gi];
+        dxG[(long long)s * nG + gi] = d;
+        const long long at = (long long)s * X.N + B.bvar_ibus[gi];
+        if (B.bvar_isT[gi]) X.xT[at] += d;
+        else X.xV[at] += d;
+        if (!isfinite(d)) bad = true;
+        mx = fmax(mx, fabs(d));
+    }
+    if (bad) atomicOr(X.err + s, 2);
+    mx = block_max(mx, red);
+    if (tid == 0) {
+        atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
+        if (s_err) atomicOr(X.err + s, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// back-substitution (Eq. backsub) + state update (FP64)
+// ---------------------------------------------------------------------------
+template <class RG, class RS>
+__global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas, Tables T, State X,
+                                              const int2 *__restrict__ inst, int area_only,
+                                              const RG *__restrict__ fac, const RS *__restrict__ cvec,
+                                              const double *__restrict__ dxG, int n_gamma) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    int k, s;
+    if (area_only >= 0) {
+        k = area_only;
+        s = blockIdx.x;
+    } else {
+        const int2 ks = inst[blockIdx.x];
+        k = ks.x;
+        s = ks.y;
+    }
+    if (!X.active[s]) return;
+    const AreaDev A = areas[k];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    RS *y = (RS *)smem;
+    const RS *c = cvec + A.c_base + (long long)s * A.F.n_int;
+    for (int i = tid; i < A.F.n_int; i += nt) y[i] = c[i];
+    for (int lv = tid; lv < A.F.n_bnd; lv += nt)
+        y[A.F.n_int + lv] = RS(dxG[(long long)s * n_gamma + T.ebnd[A.ebnd_base + lv]]);
+    __syncthreads();
+    back_solve<RG, RS>(A.F, T, fac + A.fac_base + (long long)s * A.fac_stride, y);
+    double mx = 0.0;
+    bool bad = false;
+    for (int q = tid; q < A.nb_int; q += nt) {
+        const long long at = (long long)s * X.N + T.locbus[A.bus_base + q];
+        const double dV = double(y[T.qvarV[A.bus_base + q]]);
+        X.xV[at] += dV;
+        mx = fmax(mx, fabs(dV));
+        bad |= !isfinite(dV);
+        const int vt = T.qvarT[A.bus_base + q];
+        if (vt >= 0) {
+            const double dT = double(y[vt]);
+            X.xT[at] += dT;
+            mx = fmax(mx, fabs(dT));
+            bad |= !isfinite(dT);
+        }
+    }
+    if (bad) atomicOr(X.err + s, 2);
+    mx = block_max(mx, red);
+    if (tid == 0) atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
+}
+
+// ---------------------------------------------------------------------------
+// per-snapshot bookkeeping after a step
+// ---------------------------------------------------------------------------
+struct StopRule {
+    double tol;
+    int max_iter;
+};
+
+__global__ void k_finalize(State X, int *iters, int *status, double *laststep,
+                           const StopRule *__restrict__ rule, int *n_active) {
+    const double tol = rule->tol;
+    const int max_iter = rule->max_iter;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int s = threadIdx.x; s < X.S; s += blockDim.x) {
+        if (X.active[s]) {
+            const int it = ++iters[s];
+            const double m = __longlong_as_double((long long)X.maxstep[s]);
+            laststep[s] = m;
+            const int e = X.err[s];
+            int st = -1;
+            if (e & 1) st = 2;                       // MASE_SNAP_NOT_SPD
+            else if ((e & 2) || !isfinite(m)) st = 3; // MASE_SNAP_NONFINITE
+            else if (m < tol) st = 0;                 // MASE_SNAP_CONVERGED
+            else if (it >= max_iter) st = 1;          // MASE_SNAP_MAX_ITER
+            if (st >= 0) {
+                status[s] = st;
+                X.active[s] = 0;
+            } else {
+                ++c;
+            }
+        }
+        X.maxstep[s] = 0ull;
+        X.J[s] = 0.0;
+    }
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *n_active = cnt;
+}
+
+__global__ void k_reset(State X, int *iters, int *status, double *laststep) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < X.S; s += gridDim.x * blockDim.x) {
+        X.active[s] = 1;
+        X.err[s] = 0;
+        X.J[s] = 0.0;
+        X.maxstep[s] = 0ull;
+        iters[s] = 0;
+        status[s] = 1;
+        laststep[s] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// layout conversions
+// ---------------------------------------------------------------------------
+__global__ void k_gather_rows(const double *__restrict__ src, double *__restrict__ dst,
+                              const int *__restrict__ perm, int M, int S) {
+    const long long n = (long long)M * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / M;
+        const int r = (int)(i - s * M);
+        dst[i] = src[s * M + perm[r]];
+    }
+}
+__global__ void k_gather_mask(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                              const int *__restrict__ perm, int M, int S) {
+    const long long n = (long long)M * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / M;
+        const int r = (int)(i - s * M);
+        dst[i] = src[s * M + perm[r]];
+    }
+}
+// canonical x[s][2N] <-> internal (xV, xT)[s][N]
+__global__ void k_state_in(const double *__restrict__ x, double *xV, double *xT,
+                           const int *__restrict__ bus_of_ibus, int N, int S, int flat) {
+    const long long n = (long long)N * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / N;
+        const int ib = (int)(i - s * N);
+        if (flat) {
+            xV[i] = 1.0;
+            xT[i] = 0.0;
+        } else {
+            const int b = bus_of_ibus[ib];
+            xV[i] = x[s * 2 * N + b];
+            xT[i] = x[s * 2 * N + N + b];
+        }
+    }
+}
+__global__ void k_state_out(double *__restrict__ x, const double *xV, const double *xT,
+                            const int *__restrict__ bus_of_ibus, int N, int S) {
+    const long long n = (long long)N * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / N;
+        const int ib = (int)(i - s * N);
+        const int b = bus_of_ibus[ib];
+        x[s * 2 * N + b] = xV[i];
+        x[s * 2 * N + N + b] = xT[i];
+    }
+}
+
+// h(x) in canonical order (Eq. typed_meas), one thread per bus or branch.
+__global__ void k_measure(const double *__restrict__ x, double *__restrict__ z, int N, int L, int S,
+                          const int *__restrict__ from, const int *__restrict__ to,
+                          const double *__restrict__ g, const double *__restrict__ b,
+                          const double *__restrict__ bh, const int *__restrict__ inc_beg,
+                          const int *__restrict__ inc_br) {
+    const int M = 3 * N + 4 * L;
+    const long long n = (long long)(N + L) * S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / (N + L);
+        const int u = (int)(i - s * (N + L));
+        const double *Vm = x + s * 2 * N;
+        const double *Va = Vm + N;
+        double *zs = z + s * M;
+        if (u < N) {
+            double P = 0.0, Q = 0.0, si, ci;
+            sincos(Va[u], &si, &ci);
+            for (int t = inc_beg[u]; t < inc_beg[u + 1]; ++t) {
+                const int l = inc_br[t];
+                const int j = from[l] == u ? to[l] : from[l];
+                double sj, cj;
+                sincos(Va[j], &sj, &cj);
+                const EndFlow f = end_flow(Vm[u], Vm[j], ci, si, cj, sj, g[l], b[l], bh[l]);
+                P += f.P;
+                Q += f.Q;
+            }
+            zs[u] = Vm[u];
+            zs[N + u] = P;
+            zs[2 * N + u] = Q;
+        } else {
+            const int l = u - N;
+            const int f_ = from[l], t_ = to[l];
+            double sf, cf, stt, ct;
+            sincos(Va[f_], &sf, &cf);
+            sincos(Va[t_], &stt, &ct);
+            const EndFlow a = end_flow(Vm[f_], Vm[t_], cf, sf, ct, stt, g[l], b[l], bh[l]);
+            const EndFlow c = end_flow(Vm[t_], Vm[f_], ct, stt, cf, sf, g[l], b[l], bh[l]);
+            zs[3 * N + l] = a.P;
+            zs[3 * N + L + l] = a.Q;
+            zs[3 * N + 2 * L + l] = c.P;
+            zs[3 * N + 3 * L + l] = c.Q;
+        }
+    }
+}
+
+}  // namespace mase_dev

@@ -1,0 +1,799 @@
+// C-ABI implementation of libmase (see include/mase.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mase.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+using namespace mase_dev;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(MASE_EDEVICE, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct HostTables {
+    std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_rows, sn_order, item_off, lev_items, lev_off;
+    std::vector<int> rows, colbase, relbase, rel;
+    std::vector<int> locbus, qvarV, qvarT, own_q, own_gvv, own_ebeg, own_sbeg;
+    std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
+    std::vector<double> end_g, end_b, end_bh;
+    std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
+};
+
+template <class V>
+void app(V &dst, const V &src) {
+    dst.insert(dst.end(), src.begin(), src.end());
+}
+
+FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
+    FacDev d{};
+    d.n_int = F.n_int;
+    d.n_bnd = F.n_bnd;
+    d.nsn = F.nsn();
+    d.nlev = F.nlev();
+    d.store_int = F.store_int;
+    d.store_total = F.store_total;
+    d.off_B = F.off_B;
+    d.max_w = F.max_w;
+    d.sn_base = (int)H.sn_c0.size();
+    app(H.sn_c0, F.sn_c0);
+    app(H.sn_w, F.sn_w);
+    app(H.sn_nr, F.sn_nr);
+    app(H.sn_off, F.sn_off);
+    app(H.sn_rows, F.sn_rows);
+    app(H.sn_order, F.sn_order);
+    app(H.item_off, F.item_off);
+    d.lev_base = (int)H.lev_items.size();
+    app(H.lev_items, F.lev_items);
+    d.levoff_base = (int)H.lev_off.size();
+    if (F.lev_off.empty()) H.lev_off.push_back(0);
+    else app(H.lev_off, F.lev_off);
+    d.rows_base = (int)H.rows.size();
+    app(H.rows, F.rows);
+    app(H.colbase, F.colbase);
+    app(H.relbase, F.relbase);
+    d.rel_base = (int)H.rel.size();
+    app(H.rel, F.rel);
+    return d;
+}
+
+inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t count) {
+        n = count;
+        if (!count) return cudaSuccess;
+        return cudaMalloc((void **)&p, count * sizeof(T));
+    }
+    cudaError_t upload(const std::vector<T> &v, cudaStream_t st) {
+        cudaError_t e = alloc(v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct mase_handle {
+    mase::Setup S;
+    mase_options opt{};
+    cudaStream_t stream = nullptr;
+    int n_snap = 0;
+    int start_mode = MASE_START_FLAT;
+    int smem_limit = 0;
+    int threads = 256;
+    // tables
+    HostTables H;
+    std::vector<AreaDev> areas_h;
+    BndDev bnd{};
+    DevBuf<AreaDev> d_areas;
+    DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_rows, t_sn_order, t_item_off, t_lev_items,
+        t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
+        t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
+        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd;
+    DevBuf<double> t_end_g, t_end_b, t_end_bh;
+    DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
+        b_bvar_isT;
+    Tables T{};
+    DevBuf<int2> d_inst;
+    std::vector<int2> inst_h;
+    // state and measurements
+    DevBuf<double> xV, xT, z_int, z_stage, W;
+    DevBuf<uint8_t> mask_int, mask_stage;
+    bool has_mask = false, has_z = false;
+    DevBuf<int> zperm, bus_of_ibus;
+    // work buffers
+    DevBuf<unsigned char> fac, cvec, bst, bA;
+    DevBuf<double> bh, dxG, J, laststep, xbuf;
+    DevBuf<int> active, err, iters, status, n_active;
+    DevBuf<unsigned long long> maxstep;
+    int *h_n_active = nullptr;   // pinned
+    size_t smem_local = 0, smem_back = 0, smem_bnd = 0;
+    long long fac_elems = 0, c_elems = 0, bh_elems = 0;
+    // measurement function tables (canonical numbering)
+    DevBuf<int> m_from, m_to, m_inc_beg, m_inc_br;
+    DevBuf<double> m_g, m_b, m_bh;
+    // graph
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_launches = 0;
+    DevBuf<StopRule> stop;
+    cudaStream_t user_stream = nullptr;   // caller's stream (NULL = legacy default stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    mase_info info{};
+
+    ~mase_handle() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_n_active) cudaFreeHost(h_n_active);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+// The library works on its own non-blocking stream; every call first waits
+// for work already queued on the caller's stream and, before returning,
+// makes the caller's stream wait for the library's work.
+int join_in(mase_handle *h) {
+    CK(cudaEventRecord(h->ev_in, h->user_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+    return MASE_OK;
+}
+int join_out(mase_handle *h) {
+    CK(cudaEventRecord(h->ev_out, h->stream));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+    return MASE_OK;
+}
+
+template <class RG, class RS>
+void setup_attrs(mase_handle *h) {
+    cudaFuncSetAttribute(k_local<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
+    cudaFuncSetAttribute(k_back<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
+    cudaFuncSetAttribute(k_boundary<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         h->smem_limit);
+}
+
+State make_state(mase_handle *h) {
+    State X;
+    X.N = h->S.N;
+    X.M = h->S.m;
+    X.S = h->n_snap;
+    X.xV = h->xV.p;
+    X.xT = h->xT.p;
+    X.z = h->z_int.p;
+    X.W = h->W.p;
+    X.mask = h->has_mask ? h->mask_int.p : nullptr;
+    X.active = h->active.p;
+    X.err = h->err.p;
+    X.J = h->J.p;
+    X.maxstep = h->maxstep.p;
+    return X;
+}
+
+// One Gauss-Newton step for every active snapshot: local condensation,
+// coordinator, back-substitution, bookkeeping.
+template <class RG, class RS>
+int enqueue_step(mase_handle *h, int *launches) {
+    State X = make_state(h);
+    cudaStream_t st = h->stream;
+    const int S = h->n_snap, K = h->S.K, nt = h->threads;
+    RG *fac = (RG *)h->fac.p;
+    RS *cv = (RS *)h->cvec.p;
+    if (h->opt.schedule == MASE_BATCHED) {
+        k_local<RG, RS><<<K * S, nt, h->smem_local, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1,
+                                                         MODE_FULL, fac, cv, h->bh.p);
+        ++*launches;
+    } else {
+        for (int k = 0; k < K; ++k) {
+            k_local<RG, RS><<<S, nt, h->areas_h[k].smem_bytes, st>>>(
+                h->d_areas.p, h->T, X, nullptr, k, MODE_FULL, fac, cv, h->bh.p);
+            ++*launches;
+        }
+    }
+    if (h->bnd.n_gamma > 0) {
+        k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
+                                                      (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p,
+                                                      h->opt.precision == MASE_MIXED ? h->opt.refine : 0);
+        ++*launches;
+    }
+    if (h->opt.schedule == MASE_BATCHED) {
+        k_back<RG, RS><<<K * S, nt, h->smem_back, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1, fac,
+                                                       cv, h->dxG.p, h->bnd.n_gamma);
+        ++*launches;
+    } else {
+        for (int k = 0; k < K; ++k) {
+            size_t sm = (size_t)(h->areas_h[k].F.n_int + h->areas_h[k].F.n_bnd) * sizeof(RS);
+            k_back<RG, RS><<<S, nt, sm, st>>>(h->d_areas.p, h->T, X, nullptr, k, fac, cv, h->dxG.p,
+                                             h->bnd.n_gamma);
+            ++*launches;
+        }
+    }
+    return MASE_OK;
+}
+
+int enqueue_finalize(mase_handle *h, int *launches) {
+    State X = make_state(h);
+    k_finalize<<<1, 1024, 0, h->stream>>>(X, h->iters.p, h->status.p, h->laststep.p, h->stop.p,
+                                         h->n_active.p);
+    ++*launches;
+    CK(cudaMemcpyAsync(h->h_n_active, h->n_active.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return MASE_OK;
+}
+
+template <class RG, class RS>
+int enqueue_objective(mase_handle *h, int *launches) {
+    State X = make_state(h);
+    k_local<RG, RS><<<h->S.K * h->n_snap, h->threads, h->smem_local, h->stream>>>(
+        h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (RG *)h->fac.p, (RS *)h->cvec.p,
+        h->bh.p);
+    ++*launches;
+    return MASE_OK;
+}
+
+template <class RG, class RS>
+int build(mase_handle *h) {
+    mase::Setup &S = h->S;
+    cudaStream_t st = h->stream;
+    const int K = S.K, nS = h->n_snap;
+    HostTables &H = h->H;
+    h->areas_h.resize(K);
+    size_t max_local = 0, max_back = 0;
+    long long fac_off = 0, c_off = 0, bh_off = 0;
+    int in_smem_count = 0;
+    long long factor_nnz = 0, local_flops = 0, gup = 0;
+    int max_vars = 0, max_nb = 0;
+    for (int k = 0; k < K; ++k) {
+        const mase::AreaSetup &A = S.areas[k];
+        AreaDev d{};
+        d.F = append_fac(H, A.F);
+        d.nb_int = A.nb_int;
+        d.nb_loc = A.nb_loc;
+        d.n_own = A.n_own;
+        d.n_ends = A.n_ends;
+        d.n_slots = A.n_slots;
+        d.n_items = A.n_items;
+        d.bus_base = (int)H.locbus.size();
+        app(H.locbus, A.locbus);
+        app(H.qvarV, A.qvarV);
+        app(H.qvarT, A.qvarT);
+        d.own_base = (int)H.own_q.size();
+        app(H.own_q, A.own_q);
+        app(H.own_gvv, A.own_gvv);
+        d.own1_base = (int)H.own_ebeg.size();
+        app(H.own_ebeg, A.own_ebeg);
+        app(H.own_sbeg, A.own_sbeg);
+        d.end_base = (int)H.end_qi.size();
+        app(H.end_qi, A.end_qi);
+        app(H.end_qj, A.end_qj);
+        app(H.end_own, A.end_own);
+        app(H.end_var, A.end_var);
+        app(H.end_gpos, A.end_gpos);
+        app(H.end_g, A.end_g);
+        app(H.end_b, A.end_b);
+        app(H.end_bh, A.end_bh);
+        d.slot_base = (int)H.slot_q.size();
+        app(H.slot_q, A.slot_q);
+        app(H.slot_ebeg, A.slot_ebeg);
+        app(H.slot_ecnt, A.slot_ecnt);
+        d.item_base = (int)H.item_own.size();
+        app(H.item_own, A.item_own);
+        app(H.item_uv, A.item_uv);
+        app(H.item_pos, A.item_pos);
+        d.ebnd_base = (int)H.ebnd.size();
+        app(H.ebnd, A.ebnd);
+        d.zrow_base = S.zrow_base[k];
+        // dynamic shared memory layout
+        const int nv = A.n_int + A.n_bnd;
+        const size_t endstride = std::max<size_t>(16, 4 * sizeof(RG));
+        size_t o = 0;
+        d.off_g = (int)o;
+        o = align16(o + nv * sizeof(double));
+        d.off_y = (int)o;
+        o = align16(o + nv * sizeof(RS));
+        d.off_bus = (int)o;
+        o = align16(o + 4 * (size_t)A.nb_loc * sizeof(double));
+        d.off_end = (int)o;
+        o = align16(o + (size_t)A.n_ends * endstride);
+        d.off_inj = (int)o;
+        o = align16(o + (size_t)A.n_own * 16);
+        d.off_self = (int)o;
+        o = align16(o + 4 * (size_t)A.n_own * sizeof(RG));
+        d.off_st = (int)o;
+        const size_t with_st = o + (size_t)A.F.store_total * sizeof(RG);
+        if (with_st <= (size_t)h->smem_limit) {
+            d.in_smem = 1;
+            d.smem_bytes = (int)with_st;
+            ++in_smem_count;
+        } else {
+            d.in_smem = 0;
+            d.smem_bytes = (int)o;
+        }
+        if (o > (size_t)h->smem_limit)
+            return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large for shared memory");
+        max_local = std::max(max_local, (size_t)d.smem_bytes);
+        max_back = std::max(max_back, (size_t)nv * sizeof(RS));
+        d.fac_base = fac_off;
+        d.fac_stride = A.F.store_total;
+        fac_off += (long long)A.F.store_total * nS;
+        d.c_base = c_off;
+        c_off += (long long)A.n_int * nS;
+        d.bh_base = bh_off;
+        bh_off += (long long)A.n_bnd * nS;
+        h->areas_h[k] = d;
+        factor_nnz += A.F.store_total;
+        local_flops += A.F.flops;
+        gup += A.g_updates;
+        max_vars = std::max(max_vars, nv);
+        max_nb = std::max(max_nb, A.n_bnd);
+    }
+    h->fac_elems = fac_off;
+    h->c_elems = c_off;
+    h->bh_elems = bh_off;
+    h->smem_local = max_local;
+    h->smem_back = max_back;
+    // boundary system
+    const mase::BoundarySetup &B = S.B;
+    BndDev &bd = h->bnd;
+    bd.F = append_fac(H, B.F);
+    bd.n_gamma = B.n_gamma;
+    bd.stride = B.F.store_total;
+    h->smem_bnd = (size_t)B.n_gamma * (3 * sizeof(double) + sizeof(RS)) + 16;
+    if (h->smem_bnd > (size_t)h->smem_limit)
+        return set_err(MASE_EINVAL, "boundary system too large for shared-memory vectors");
+    // instance list: areas by descending work, snapshots innermost
+    std::vector<int> ord(K);
+    for (int k = 0; k < K; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int a, int b) { return S.areas[a].work > S.areas[b].work; });
+    h->inst_h.clear();
+    for (int k : ord)
+        for (int s = 0; s < nS; ++s) h->inst_h.push_back(make_int2(k, s));
+    // uploads
+#define UP(buf, vec) CK(h->buf.upload(H.vec, st))
+    UP(t_sn_c0, sn_c0); UP(t_sn_w, sn_w); UP(t_sn_nr, sn_nr); UP(t_sn_off, sn_off);
+    UP(t_sn_rows, sn_rows); UP(t_sn_order, sn_order); UP(t_item_off, item_off);
+    UP(t_lev_items, lev_items); UP(t_lev_off, lev_off); UP(t_rows, rows); UP(t_colbase, colbase);
+    UP(t_relbase, relbase); UP(t_rel, rel); UP(t_locbus, locbus); UP(t_qvarV, qvarV);
+    UP(t_qvarT, qvarT); UP(t_own_q, own_q); UP(t_own_gvv, own_gvv); UP(t_own_ebeg, own_ebeg);
+    UP(t_own_sbeg, own_sbeg); UP(t_end_qi, end_qi); UP(t_end_qj, end_qj); UP(t_end_own, end_own);
+    UP(t_end_var, end_var); UP(t_end_gpos, end_gpos); UP(t_end_g, end_g); UP(t_end_b, end_b);
+    UP(t_end_bh, end_bh); UP(t_slot_q, slot_q); UP(t_slot_ebeg, slot_ebeg);
+    UP(t_slot_ecnt, slot_ecnt); UP(t_item_own, item_own); UP(t_item_uv, item_uv);
+    UP(t_item_pos, item_pos); UP(t_ebnd, ebnd);
+#undef UP
+    CK(h->b_asm_beg.upload(B.asm_beg, st));
+    CK(h->b_asm_area.upload(B.asm_area, st));
+    CK(h->b_asm_off.upload(B.asm_off, st));
+    CK(h->b_rhs_beg.upload(B.rhs_beg, st));
+    CK(h->b_rhs_area.upload(B.rhs_area, st));
+    CK(h->b_rhs_lv.upload(B.rhs_lv, st));
+    CK(h->b_bvar_ibus.upload(B.bvar_ibus, st));
+    CK(h->b_bvar_isT.upload(B.bvar_isT, st));
+    bd.asm_beg = h->b_asm_beg.p;
+    bd.asm_area = h->b_asm_area.p;
+    bd.asm_off = h->b_asm_off.p;
+    bd.rhs_beg = h->b_rhs_beg.p;
+    bd.rhs_area = h->b_rhs_area.p;
+    bd.rhs_lv = h->b_rhs_lv.p;
+    bd.bvar_ibus = h->b_bvar_ibus.p;
+    bd.bvar_isT = h->b_bvar_isT.p;
+    std::vector<AreaDev> ah = h->areas_h;
+    CK(h->d_areas.upload(ah, st));
+    CK(h->d_inst.upload(h->inst_h, st));
+    Tables &T = h->T;
+    T.sn_c0 = h->t_sn_c0.p; T.sn_w = h->t_sn_w.p; T.sn_nr = h->t_sn_nr.p; T.sn_off = h->t_sn_off.p;
+    T.sn_rows = h->t_sn_rows.p; T.sn_order = h->t_sn_order.p; T.item_off = h->t_item_off.p;
+    T.lev_items = h->t_lev_items.p; T.lev_off = h->t_lev_off.p; T.rows = h->t_rows.p;
+    T.colbase = h->t_colbase.p; T.relbase = h->t_relbase.p; T.rel = h->t_rel.p;
+    T.locbus = h->t_locbus.p; T.qvarV = h->t_qvarV.p; T.qvarT = h->t_qvarT.p;
+    T.own_q = h->t_own_q.p; T.own_gvv = h->t_own_gvv.p; T.own_ebeg = h->t_own_ebeg.p;
+    T.own_sbeg = h->t_own_sbeg.p; T.end_qi = h->t_end_qi.p; T.end_qj = h->t_end_qj.p;
+    T.end_own = h->t_end_own.p; T.end_var = h->t_end_var.p; T.end_gpos = h->t_end_gpos.p;
+    T.end_g = h->t_end_g.p; T.end_b = h->t_end_b.p; T.end_bh = h->t_end_bh.p;
+    T.slot_q = h->t_slot_q.p; T.slot_ebeg = h->t_slot_ebeg.p; T.slot_ecnt = h->t_slot_ecnt.p;
+    T.item_own = h->t_item_own.p; T.item_uv = h->t_item_uv.p; T.item_pos = h->t_item_pos.p;
+    T.ebnd = h->t_ebnd.p;
+    // work buffers
+    CK(h->fac.alloc((size_t)h->fac_elems * sizeof(RG)));
+    CK(h->cvec.alloc((size_t)std::max<long long>(1, h->c_elems) * sizeof(RS)));
+    CK(h->bh.alloc((size_t)std::max<long long>(1, h->bh_elems)));
+    CK(h->bst.alloc((size_t)std::max(1, B.F.store_total) * nS * sizeof(RG)));
+    CK(h->bA.alloc((size_t)std::max(1, B.F.store_total) * nS * sizeof(RG)));
+    CK(h->dxG.alloc((size_t)std::max(1, B.n_gamma) * nS));
+    setup_attrs<RG, RS>(h);
+    // info
+    mase_info &I = h->info;
+    I.n_bus = S.N;
+    I.n_branch = S.L;
+    I.n_area = S.K;
+    I.n_snap = nS;
+    I.n_meas = S.m;
+    I.n_state = 2 * S.N - 1;
+    I.n_boundary_bus = S.n_boundary_bus;
+    I.n_gamma = B.n_gamma;
+    I.max_area_vars = max_vars;
+    I.max_area_nb = max_nb;
+    I.factor_nnz = factor_nnz;
+    I.local_flops = local_flops;
+    I.boundary_flops = B.F.flops;
+    I.g_updates = gup;
+    I.smem_bytes_max = (int)max_local;
+    I.areas_in_smem = in_smem_count;
+    return MASE_OK;
+}
+
+int upload_measurements(mase_handle *h, const mase_measurements *meas) {
+    cudaStream_t st = h->stream;
+    const int M = h->S.m, nS = h->n_snap;
+    const size_t n = (size_t)M * nS;
+    if (meas->z) {
+        const double *src = meas->z;
+        if (!is_device_ptr(meas->z)) {
+            CK(cudaMemcpyAsync(h->z_stage.p, meas->z, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            src = h->z_stage.p;
+        }
+        k_gather_rows<<<1024, 256, 0, st>>>(src, h->z_int.p, h->zperm.p, M, nS);
+        CK(cudaGetLastError());
+        h->has_z = true;
+    }
+    if (meas->mask) {
+        if (!h->mask_int.p) {
+            CK(h->mask_int.alloc(n));
+            CK(h->mask_stage.alloc(n));
+        }
+        const uint8_t *src = meas->mask;
+        if (!is_device_ptr(meas->mask)) {
+            CK(cudaMemcpyAsync(h->mask_stage.p, meas->mask, n, cudaMemcpyHostToDevice, st));
+            src = h->mask_stage.p;
+        }
+        k_gather_mask<<<1024, 256, 0, st>>>(src, h->mask_int.p, h->zperm.p, M, nS);
+        CK(cudaGetLastError());
+        h->has_mask = true;
+    }
+    CK(cudaStreamSynchronize(st));
+    return MASE_OK;
+}
+
+template <class RG, class RS>
+int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, double *x_out,
+               mase_stats *stats) {
+    cudaStream_t st = h->stream;
+    const int N = h->S.N, nS = h->n_snap;
+    int launches = 0;
+    State X = make_state(h);
+    k_reset<<<(nS + 255) / 256, 256, 0, st>>>(X, h->iters.p, h->status.p, h->laststep.p);
+    ++launches;
+    if (x0) {
+        const double *src = x0;
+        if (!is_device_ptr(x0)) {
+            CK(cudaMemcpyAsync(h->xbuf.p, x0, (size_t)2 * N * nS * sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+            src = h->xbuf.p;
+        }
+        k_state_in<<<1024, 256, 0, st>>>(src, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS, 0);
+    } else {
+        k_state_in<<<1024, 256, 0, st>>>(nullptr, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS, 1);
+    }
+    ++launches;
+    CK(cudaGetLastError());
+    StopRule rule{tol, max_iter};
+    CK(cudaMemcpyAsync(h->stop.p, &rule, sizeof(rule), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    for (int it = 0; it < max_iter; ++it) {
+        if (h->opt.use_graph) {
+            if (!h->graph_exec) {
+                int per_step = 0;
+                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                int rc = enqueue_step<RG, RS>(h, &per_step);
+                int rc2 = enqueue_finalize(h, &per_step);
+                cudaGraph_t g = nullptr;
+                cudaError_t ce = cudaStreamEndCapture(st, &g);
+                if (rc != MASE_OK) return rc;
+                if (rc2 != MASE_OK) return rc2;
+                CK(ce);
+                h->graph = g;
+                h->graph_launches = per_step;
+                CK(cudaGraphInstantiate(&h->graph_exec, g, 0));
+            }
+            CK(cudaGraphLaunch(h->graph_exec, st));
+            launches += h->graph_launches;
+        } else {
+            int rc = enqueue_step<RG, RS>(h, &launches);
+            if (rc != MASE_OK) return rc;
+            rc = enqueue_finalize(h, &launches);
+            if (rc != MASE_OK) return rc;
+        }
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        if (*h->h_n_active == 0) break;
+    }
+    int rc = enqueue_objective<RG, RS>(h, &launches);
+    if (rc != MASE_OK) return rc;
+    if (x_out) {
+        if (is_device_ptr(x_out)) {
+            k_state_out<<<1024, 256, 0, st>>>(x_out, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
+        } else {
+            k_state_out<<<1024, 256, 0, st>>>(h->xbuf.p, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
+            CK(cudaMemcpyAsync(x_out, h->xbuf.p, (size_t)2 * N * nS * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+        }
+        ++launches;
+    }
+    std::vector<int> iters(nS), status(nS);
+    std::vector<double> J(nS), last(nS);
+    CK(cudaMemcpyAsync(iters.data(), h->iters.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(status.data(), h->status.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(J.data(), h->J.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(last.data(), h->laststep.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    int ret = MASE_OK;
+    for (int s = 0; s < nS; ++s) {
+        if (status[s] == MASE_SNAP_MAX_ITER && ret == MASE_OK) ret = MASE_NOT_CONVERGED;
+        if (status[s] == MASE_SNAP_NOT_SPD) ret = MASE_EUNOBSERVABLE;
+        if (status[s] == MASE_SNAP_NONFINITE && ret != MASE_EUNOBSERVABLE) ret = MASE_ENONFINITE;
+    }
+    if (stats) {
+        for (int s = 0; s < nS; ++s) {
+            if (stats->iters) stats->iters[s] = iters[s];
+            if (stats->status) stats->status[s] = status[s];
+            if (stats->J) stats->J[s] = J[s];
+            if (stats->max_step) stats->max_step[s] = last[s];
+        }
+        stats->total_launches = launches;
+    }
+    if (ret == MASE_EUNOBSERVABLE) set_err(ret, "non-positive pivot in an area or boundary factor");
+    if (ret == MASE_ENONFINITE) set_err(ret, "non-finite step");
+    return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mase_default_options(mase_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = MASE_MIXED;
+    o->schedule = MASE_BATCHED;
+    o->use_graph = 1;
+    o->refine = 1;
+    o->threads = 0;
+    o->device = 0;
+    o->stream = nullptr;
+}
+
+const char *mase_status_str(int code) {
+    switch (code) {
+        case MASE_OK: return "MASE_OK";
+        case MASE_NOT_CONVERGED: return "MASE_NOT_CONVERGED";
+        case MASE_EINVAL: return "MASE_EINVAL";
+        case MASE_EUNOBSERVABLE: return "MASE_EUNOBSERVABLE";
+        case MASE_ENONFINITE: return "MASE_ENONFINITE";
+        case MASE_EDEVICE: return "MASE_EDEVICE";
+        case MASE_ENOTREADY: return "MASE_ENOTREADY";
+        default: return "MASE_UNKNOWN";
+    }
+}
+
+const char *mase_last_error(void) { return g_last_error.c_str(); }
+
+int mase_create(const mase_network *net, const mase_partition *part, const mase_measurements *meas,
+                const mase_options *opt, mase_handle **out) {
+    if (!net || !part || !meas || !out) return set_err(MASE_EINVAL, "null argument");
+    if (meas->n_snap < 1) return set_err(MASE_EINVAL, "n_snap must be >= 1");
+    if (!meas->sigma) return set_err(MASE_EINVAL, "sigma is required");
+    std::unique_ptr<mase_handle> h(new mase_handle());
+    if (opt) h->opt = *opt;
+    else mase_default_options(&h->opt);
+    if (h->opt.precision != MASE_FP64 && h->opt.precision != MASE_MIXED)
+        return set_err(MASE_EINVAL, "bad precision");
+    if (h->opt.schedule != MASE_PER_AREA && h->opt.schedule != MASE_BATCHED)
+        return set_err(MASE_EINVAL, "bad schedule");
+    if (h->opt.refine < 0 || h->opt.refine > 8) return set_err(MASE_EINVAL, "bad refine count");
+    int threads = h->opt.threads ? h->opt.threads : 256;
+    if (threads < 64 || threads > 512 || threads % 32) return set_err(MASE_EINVAL, "bad threads");
+    h->threads = threads;
+    mase::NetIn ni{net->n_bus, net->n_branch, net->slack_bus, net->from_bus, net->to_bus,
+                   net->r, net->x, net->b_charge};
+    if (!mase::build_setup(ni, part->n_area, part->area_of_bus, h->S))
+        return set_err(MASE_EINVAL, h->S.error);
+    const int M = h->S.m;
+    for (int i = 0; i < M; ++i)
+        if (!(meas->sigma[i] > 0.0) || !std::isfinite(meas->sigma[i]))
+            return set_err(MASE_EINVAL, "sigma must be positive and finite");
+    CK(cudaSetDevice(h->opt.device));
+    h->user_stream = (cudaStream_t)h->opt.stream;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    {
+        int rc0 = join_in(h.get());
+        if (rc0 != MASE_OK) return rc0;
+    }
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->opt.device));
+    h->smem_limit = optin - 1024;
+    h->n_snap = meas->n_snap;
+    const int N = h->S.N, nS = h->n_snap;
+    int rc = h->opt.precision == MASE_MIXED ? build<float, float>(h.get())
+                                            : build<double, double>(h.get());
+    if (rc != MASE_OK) return rc;
+    cudaStream_t st = h->stream;
+    // state, measurement and bookkeeping buffers
+    CK(h->xV.alloc((size_t)N * nS));
+    CK(h->xT.alloc((size_t)N * nS));
+    CK(h->xbuf.alloc((size_t)2 * N * nS));
+    CK(h->z_int.alloc((size_t)M * nS));
+    CK(h->z_stage.alloc((size_t)M * nS));
+    std::vector<double> Wh(M);
+    for (int i = 0; i < M; ++i) {
+        const double sg = meas->sigma[h->S.zperm[i]];
+        Wh[i] = 1.0 / (sg * sg);
+    }
+    CK(h->W.upload(Wh, st));
+    CK(h->zperm.upload(h->S.zperm, st));
+    CK(h->bus_of_ibus.upload(h->S.bus_of_ibus, st));
+    CK(h->active.alloc(nS));
+    CK(h->err.alloc(nS));
+    CK(h->iters.alloc(nS));
+    CK(h->status.alloc(nS));
+    CK(h->n_active.alloc(1));
+    CK(h->J.alloc(nS));
+    CK(h->laststep.alloc(nS));
+    CK(h->maxstep.alloc(nS));
+    CK(h->stop.alloc(1));
+    CK(cudaMallocHost((void **)&h->h_n_active, sizeof(int)));
+    // measurement-function tables in canonical numbering
+    {
+        const int L = h->S.L;
+        std::vector<int> fr(net->from_bus, net->from_bus + L), to(net->to_bus, net->to_bus + L);
+        std::vector<double> g(L), b(L), bh(L);
+        for (int l = 0; l < L; ++l) {
+            const double den = net->r[l] * net->r[l] + net->x[l] * net->x[l];
+            g[l] = net->r[l] / den;
+            b[l] = -net->x[l] / den;
+            bh[l] = 0.5 * net->b_charge[l];
+        }
+        std::vector<int> beg(N + 1, 0), br;
+        for (int l = 0; l < L; ++l) {
+            ++beg[fr[l] + 1];
+            ++beg[to[l] + 1];
+        }
+        for (int i = 0; i < N; ++i) beg[i + 1] += beg[i];
+        br.assign(beg[N], 0);
+        std::vector<int> fill(beg.begin(), beg.end() - 1);
+        for (int l = 0; l < L; ++l) {
+            br[fill[fr[l]]++] = l;
+            br[fill[to[l]]++] = l;
+        }
+        CK(h->m_from.upload(fr, st));
+        CK(h->m_to.upload(to, st));
+        CK(h->m_g.upload(g, st));
+        CK(h->m_b.upload(b, st));
+        CK(h->m_bh.upload(bh, st));
+        CK(h->m_inc_beg.upload(beg, st));
+        CK(h->m_inc_br.upload(br, st));
+    }
+    rc = upload_measurements(h.get(), meas);
+    if (rc != MASE_OK) return rc;
+    CK(cudaStreamSynchronize(st));
+    rc = join_out(h.get());
+    if (rc != MASE_OK) return rc;
+    *out = h.release();
+    return MASE_OK;
+}
+
+int mase_set_measurements(mase_handle *h, const mase_measurements *meas) {
+    if (!h || !meas) return set_err(MASE_EINVAL, "null argument");
+    if (meas->n_snap != h->n_snap) return set_err(MASE_EINVAL, "n_snap differs from the handle's");
+    CK(cudaSetDevice(h->opt.device));
+    int rc = join_in(h);
+    if (rc != MASE_OK) return rc;
+    rc = upload_measurements(h, meas);
+    int rc2 = join_out(h);
+    return rc != MASE_OK ? rc : rc2;
+}
+
+int mase_solve(mase_handle *h, const double *x0, double tol, int32_t max_iter, double *x_out,
+               mase_stats *stats) {
+    if (!h) return set_err(MASE_EINVAL, "null handle");
+    if (!h->has_z) return set_err(MASE_ENOTREADY, "no measurements set");
+    if (max_iter < 1 || max_iter > 1000) return set_err(MASE_EINVAL, "max_iter out of range");
+    if (!(tol >= 0.0)) return set_err(MASE_EINVAL, "tol must be >= 0");
+    CK(cudaSetDevice(h->opt.device));
+    int rc = join_in(h);
+    if (rc != MASE_OK) return rc;
+    rc = h->opt.precision == MASE_MIXED ? solve_impl<float, float>(h, x0, tol, max_iter, x_out, stats)
+                                        : solve_impl<double, double>(h, x0, tol, max_iter, x_out, stats);
+    int rc2 = join_out(h);
+    return rc != MASE_OK ? rc : rc2;
+}
+
+int mase_measure(mase_handle *h, const double *x, int32_t n_snap, double *z_out) {
+    if (!h || !x || !z_out || n_snap < 1) return set_err(MASE_EINVAL, "bad argument");
+    CK(cudaSetDevice(h->opt.device));
+    {
+        int rc0 = join_in(h);
+        if (rc0 != MASE_OK) return rc0;
+    }
+    cudaStream_t st = h->stream;
+    const int N = h->S.N, L = h->S.L, M = h->S.m;
+    const bool dx = is_device_ptr(x), dz = is_device_ptr(z_out);
+    DevBuf<double> xs, zs;
+    const double *xd = x;
+    double *zd = z_out;
+    if (!dx) {
+        CK(xs.alloc((size_t)2 * N * n_snap));
+        CK(cudaMemcpyAsync(xs.p, x, (size_t)2 * N * n_snap * sizeof(double), cudaMemcpyHostToDevice, st));
+        xd = xs.p;
+    }
+    if (!dz) {
+        CK(zs.alloc((size_t)M * n_snap));
+        zd = zs.p;
+    }
+    k_measure<<<2048, 256, 0, st>>>(xd, zd, N, L, n_snap, h->m_from.p, h->m_to.p, h->m_g.p,
+                                    h->m_b.p, h->m_bh.p, h->m_inc_beg.p, h->m_inc_br.p);
+    CK(cudaGetLastError());
+    if (!dz)
+        CK(cudaMemcpyAsync(z_out, zd, (size_t)M * n_snap * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return join_out(h);
+}
+
+int mase_get_info(const mase_handle *h, mase_info *info) {
+    if (!h || !info) return set_err(MASE_EINVAL, "null argument");
+    *info = h->info;
+    return MASE_OK;
+}
+
+int mase_set_start_mode(mase_handle *h, int32_t mode) {
+    if (!h) return set_err(MASE_EINVAL, "null handle");
+    if (mode != MASE_START_FLAT && mode != MASE_START_X0 && mode != MASE_START_LEARNED)
+        return set_err(MASE_EINVAL, "bad start mode");
+    h->start_mode = mode;
+    return MASE_OK;
+}
+
+void mase_destroy(mase_handle *h) { delete h; }
+
+}  // extern "C"

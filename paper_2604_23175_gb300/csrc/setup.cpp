@@ -1,0 +1,892 @@
+// Host-side symbolic setup (see setup.h).
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <stdexcept>
+
+namespace mase {
+
+namespace {
+
+[[noreturn]] void fail(const std::string &m) { throw std::runtime_error(m); }
+
+inline int packed_col_start(int cb, int nb) { return cb * nb - cb * (cb - 1) / 2; }
+
+}  // namespace
+
+int SymFactor::pos(int r, int c) const {
+    if (r < c) std::swap(r, c);
+    if (c >= n_int) {
+        int rb = r - n_int, cb = c - n_int;
+        return off_B + packed_col_start(cb, n_bnd) + (rb - cb);
+    }
+    int t = var_sn[c];
+    int c0 = sn_c0[t], w = sn_w[t], nr = sn_nr[t];
+    int ld = w + nr;
+    int rp;
+    if (r < c0 + w) {
+        rp = r - c0;
+    } else {
+        const int *b = rows.data() + sn_rows[t];
+        const int *e = b + nr;
+        const int *it = std::lower_bound(b, e, r);
+        if (it == e || *it != r) return -1;
+        rp = w + (int)(it - b);
+    }
+    return sn_off[t] + (c - c0) * ld + rp;
+}
+
+SymResult build_symbolic(const BusSystem &sys) {
+    const int ni = sys.nb_int, nbn = sys.nb_bnd, n = ni + nbn;
+    SymResult out;
+    // --- exact minimum degree on the elimination graph (dense bitmap) ---
+    std::vector<uint8_t> A((size_t)n * n, 0);
+    std::vector<int> deg(n, 0);
+    for (int v = 0; v < n; ++v)
+        for (int u : sys.adj[v])
+            if (u != v && !A[(size_t)v * n + u]) {
+                A[(size_t)v * n + u] = A[(size_t)u * n + v] = 1;
+                ++deg[v];
+                ++deg[u];
+            }
+    std::vector<char> elim(n, 0);
+    std::vector<std::vector<int>> snodes(n);
+    std::vector<int> nb;
+    out.order.reserve(n);
+    for (int step = 0; step < ni; ++step) {
+        int best = -1;
+        for (int v = 0; v < ni; ++v)
+            if (!elim[v] && (best < 0 || deg[v] < deg[best])) best = v;
+        nb.clear();
+        const uint8_t *row = A.data() + (size_t)best * n;
+        for (int u = 0; u < n; ++u)
+            if (!elim[u] && row[u]) nb.push_back(u);
+        snodes[best] = nb;
+        for (int a : nb) {
+            A[(size_t)a * n + best] = A[(size_t)best * n + a] = 0;
+            --deg[a];
+        }
+        for (size_t i = 0; i < nb.size(); ++i)
+            for (size_t j = i + 1; j < nb.size(); ++j) {
+                int a = nb[i], b = nb[j];
+                if (!A[(size_t)a * n + b]) {
+                    A[(size_t)a * n + b] = A[(size_t)b * n + a] = 1;
+                    ++deg[a];
+                    ++deg[b];
+                }
+            }
+        elim[best] = 1;
+        out.order.push_back(best);
+    }
+    for (int v = ni; v < n; ++v) out.order.push_back(v);
+    out.pos_of.assign(n, -1);
+    for (int p = 0; p < n; ++p) out.pos_of[out.order[p]] = p;
+    out.var0.assign(n + 1, 0);
+    for (int p = 0; p < n; ++p) out.var0[p + 1] = out.var0[p] + sys.nvar[out.order[p]];
+
+    // --- structure in positions, elimination tree ---
+    std::vector<std::vector<int>> S(ni);
+    std::vector<int> parent(ni, -1), nchild(ni, 0);
+    for (int p = 0; p < ni; ++p) {
+        for (int u : snodes[out.order[p]]) S[p].push_back(out.pos_of[u]);
+        std::sort(S[p].begin(), S[p].end());
+        if (!S[p].empty() && S[p][0] <= p) fail("symbolic: structure not above diagonal");
+        if (!S[p].empty() && S[p][0] < ni) {
+            parent[p] = S[p][0];
+            ++nchild[S[p][0]];
+        }
+    }
+    // --- fundamental supernodes over buses ---
+    std::vector<int> sn_first;
+    for (int p = 0; p < ni; ++p) {
+        bool merge = false;
+        if (p > 0 && parent[p - 1] == p && nchild[p] == 1 &&
+            S[p - 1].size() == S[p].size() + 1 &&
+            std::equal(S[p].begin(), S[p].end(), S[p - 1].begin() + 1))
+            merge = true;
+        if (!merge) sn_first.push_back(p);
+    }
+    sn_first.push_back(ni);
+    const int nsn = (int)sn_first.size() - 1;
+    std::vector<int> bus_sn(ni, -1);
+    SymFactor &F = out.F;
+    F.n_int = out.var0[ni];
+    F.n_bnd = out.var0[n] - out.var0[ni];
+    F.var_sn.assign(F.n_int, -1);
+    int off = 0;
+    for (int s = 0; s < nsn; ++s) {
+        int p0 = sn_first[s], p1 = sn_first[s + 1];
+        for (int p = p0; p < p1; ++p) bus_sn[p] = s;
+        int c0 = out.var0[p0], w = out.var0[p1] - c0;
+        F.sn_c0.push_back(c0);
+        F.sn_w.push_back(w);
+        F.sn_rows.push_back((int)F.rows.size());
+        for (int q : S[p1 - 1])
+            for (int v = out.var0[q]; v < out.var0[q + 1]; ++v) F.rows.push_back(v);
+        int nr = (int)F.rows.size() - F.sn_rows.back();
+        F.sn_nr.push_back(nr);
+        F.sn_off.push_back(off);
+        off += w * (w + nr);
+        for (int c = c0; c < c0 + w; ++c) F.var_sn[c] = s;
+        F.max_w = std::max(F.max_w, w);
+    }
+    F.store_int = off;
+    F.off_B = off;
+    F.store_total = off + F.n_bnd * (F.n_bnd + 1) / 2;
+
+    // --- level schedule of the supernodal elimination tree ---
+    std::vector<int> level(nsn, 0);
+    for (int s = 0; s < nsn; ++s) {
+        int plast = sn_first[s + 1] - 1;
+        if (!S[plast].empty() && S[plast][0] < ni) {
+            int t = bus_sn[S[plast][0]];
+            if (t <= s) fail("symbolic: supernode parent not later");
+            level[t] = std::max(level[t], level[s] + 1);
+        }
+    }
+    int nlev = nsn ? *std::max_element(level.begin(), level.end()) + 1 : 0;
+    F.sn_order.resize(nsn);
+    std::iota(F.sn_order.begin(), F.sn_order.end(), 0);
+    std::stable_sort(F.sn_order.begin(), F.sn_order.end(),
+                     [&](int a, int b) { return level[a] < level[b]; });
+    F.lev_off.assign(nlev + 1, 0);
+    for (int s = 0; s < nsn; ++s) ++F.lev_off[level[s] + 1];
+    for (int l = 0; l < nlev; ++l) F.lev_off[l + 1] += F.lev_off[l];
+    F.item_off.assign(nsn, 0);
+    F.lev_items.assign(nlev, 0);
+    for (int l = 0; l < nlev; ++l) {
+        int acc = 0;
+        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
+            int s = F.sn_order[i];
+            long long R = F.sn_nr[s];
+            F.item_off[i] = acc;
+            acc += (int)(R * (R + 1) / 2 + R);
+        }
+        F.lev_items[l] = acc;
+    }
+
+    // --- update maps: target column base + relative row positions ---
+    F.colbase.assign(F.rows.size(), 0);
+    F.relbase.assign(F.rows.size(), 0);
+    for (int s = 0; s < nsn; ++s) {
+        const int R = F.sn_nr[s], rb = F.sn_rows[s], w = F.sn_w[s];
+        int cur_t = -2, relstart = 0, seg_j0 = 0;
+        for (int j = 0; j < R; ++j) {
+            int c = F.rows[rb + j];
+            int t = c < F.n_int ? F.var_sn[c] : -1;
+            if (t != cur_t) {
+                cur_t = t;
+                seg_j0 = j;
+                relstart = (int)F.rel.size();
+                for (int i = j; i < R; ++i) {
+                    int r = F.rows[rb + i];
+                    if (t >= 0) {
+                        int c0t = F.sn_c0[t], wt = F.sn_w[t];
+                        int rp;
+                        if (r < c0t + wt) {
+                            rp = r - c0t;
+                        } else {
+                            const int *b = F.rows.data() + F.sn_rows[t];
+                            const int *e = b + F.sn_nr[t];
+                            const int *it = std::lower_bound(b, e, r);
+                            if (it == e || *it != r) fail("symbolic: row not in target supernode");
+                            rp = wt + (int)(it - b);
+                        }
+                        F.rel.push_back(rp);
+                    } else {
+                        F.rel.push_back(r - F.n_int);
+                    }
+                }
+            }
+            if (t >= 0) {
+                int ld = F.sn_w[t] + F.sn_nr[t];
+                F.colbase[rb + j] = F.sn_off[t] + (c - F.sn_c0[t]) * ld;
+            } else {
+                int cb = c - F.n_int;
+                F.colbase[rb + j] = F.off_B + packed_col_start(cb, F.n_bnd) - cb;
+            }
+            F.relbase[rb + j] = relstart - seg_j0;
+        }
+        // cost of the supernode: panel factorisation + update of ancestors
+        const int ld = w + R;
+        for (int c = 0; c < w; ++c)
+            for (int c2 = c + 1; c2 < w; ++c2) F.flops += ld - c2;
+        F.flops += (long long)w * R * (R + 1) / 2;
+        F.pairs += (long long)R * (R + 1) / 2;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+
+bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st) {
+    try {
+        const int N = net.n_bus, L = net.n_branch;
+        if (N < 2 || L < 1) fail("need at least 2 buses and 1 branch");
+        if (K < 1 || K > N) fail("n_area out of range");
+        if (net.slack < 0 || net.slack >= N) fail("slack bus out of range");
+        if (!net.from || !net.to || !net.r || !net.x || !net.bc || !area_of_bus)
+            fail("null network or partition array");
+        st.N = N;
+        st.L = L;
+        st.K = K;
+        st.slack = net.slack;
+        st.m = 3 * N + 4 * L;
+        std::vector<std::vector<int>> inc(N);   // incident branches
+        for (int l = 0; l < L; ++l) {
+            int f = net.from[l], t = net.to[l];
+            if (f < 0 || f >= N || t < 0 || t >= N) fail("branch bus index out of range");
+            if (f == t) fail("branch with from == to");
+            if (!std::isfinite(net.r[l]) || !std::isfinite(net.x[l]) || !std::isfinite(net.bc[l]))
+                fail("non-finite branch parameter");
+            if (net.r[l] * net.r[l] + net.x[l] * net.x[l] <= 0.0) fail("zero series impedance");
+            inc[f].push_back(l);
+            inc[t].push_back(l);
+        }
+        std::vector<int> area(N);
+        std::vector<int> count(K, 0);
+        for (int b = 0; b < N; ++b) {
+            int a = area_of_bus[b];
+            if (a < 0 || a >= K) fail("area index out of range");
+            area[b] = a;
+            ++count[a];
+        }
+        for (int k = 0; k < K; ++k)
+            if (!count[k]) fail("empty area");
+        for (int b = 0; b < N; ++b)
+            if (inc[b].empty()) fail("isolated bus");
+        std::vector<char> bnd(N, 0);
+        for (int l = 0; l < L; ++l)
+            if (area[net.from[l]] != area[net.to[l]]) bnd[net.from[l]] = bnd[net.to[l]] = 1;
+        auto other = [&](int l, int b) { return net.from[l] == b ? net.to[l] : net.from[l]; };
+        auto nvar_of = [&](int b) { return b == net.slack ? 1 : 2; };
+
+        // ---------------- pass 1: per-area symbolic factor + internal numbering
+        std::vector<std::vector<int>> own(K), lbuses(K), nodes(K);
+        for (int b = 0; b < N; ++b) own[area[b]].push_back(b);
+        std::vector<SymResult> sym(K);
+        std::vector<int> node_of(N, -1);
+        st.areas.resize(K);
+        st.ibus_of_bus.assign(N, -1);
+        int next_ibus = 0;
+        for (int k = 0; k < K; ++k) {
+            std::vector<int> intern, lb;
+            for (int b : own[k]) {
+                if (!bnd[b]) intern.push_back(b);
+                else lb.push_back(b);
+                for (int l : inc[b]) {
+                    int o = other(l, b);
+                    if (area[o] != k) lb.push_back(o);
+                }
+            }
+            std::sort(lb.begin(), lb.end());
+            lb.erase(std::unique(lb.begin(), lb.end()), lb.end());
+            std::vector<int> &nd = nodes[k];
+            nd = intern;
+            nd.insert(nd.end(), lb.begin(), lb.end());
+            lbuses[k] = lb;
+            for (int i = 0; i < (int)nd.size(); ++i) node_of[nd[i]] = i;
+            BusSystem sys;
+            sys.nb_int = (int)intern.size();
+            sys.nb_bnd = (int)lb.size();
+            sys.adj.assign(nd.size(), {});
+            sys.nvar.resize(nd.size());
+            for (int i = 0; i < (int)nd.size(); ++i) sys.nvar[i] = nvar_of(nd[i]);
+            for (int b : own[k]) {
+                std::vector<int> cl{node_of[b]};
+                for (int l : inc[b]) cl.push_back(node_of[other(l, b)]);
+                for (int a : cl)
+                    for (int c : cl)
+                        if (a != c) sys.adj[a].push_back(c);
+            }
+            for (auto &v : sys.adj) {
+                std::sort(v.begin(), v.end());
+                v.erase(std::unique(v.begin(), v.end()), v.end());
+            }
+            sym[k] = build_symbolic(sys);
+            for (int i = 0; i < (int)nd.size(); ++i) node_of[nd[i]] = -1;
+            // internal numbering: internal buses in elimination order, then own boundary buses
+            const int ni = sys.nb_int;
+            for (int p = 0; p < ni; ++p) st.ibus_of_bus[nd[sym[k].order[p]]] = next_ibus++;
+            for (int p = ni; p < (int)nd.size(); ++p) {
+                int b = nd[sym[k].order[p]];
+                if (area[b] == k) st.ibus_of_bus[b] = next_ibus++;
+            }
+        }
+        if (next_ibus != N) fail("internal numbering incomplete");
+        st.bus_of_ibus.assign(N, -1);
+        st.area_of_ibus.assign(N, -1);
+        for (int b = 0; b < N; ++b) {
+            st.bus_of_ibus[st.ibus_of_bus[b]] = b;
+            st.area_of_ibus[st.ibus_of_bus[b]] = area[b];
+        }
+
+        // ---------------- boundary system (Sec. 3.2, 4.4)
+        std::vector<int> bbus;
+        for (int b = 0; b < N; ++b)
+            if (bnd[b]) bbus.push_back(b);
+        st.n_boundary_bus = (int)bbus.size();
+        BoundarySetup &B = st.B;
+        B.n_bbus = (int)bbus.size();
+        std::vector<int> bnode(N, -1);
+        for (int i = 0; i < (int)bbus.size(); ++i) bnode[bbus[i]] = i;
+        SymResult bsym;
+        if (!bbus.empty()) {
+            BusSystem bs;
+            bs.nb_int = (int)bbus.size();
+            bs.nb_bnd = 0;
+            bs.adj.assign(bbus.size(), {});
+            bs.nvar.resize(bbus.size());
+            for (int i = 0; i < (int)bbus.size(); ++i) bs.nvar[i] = nvar_of(bbus[i]);
+            for (int k = 0; k < K; ++k)
+                for (int a : lbuses[k])
+                    for (int c : lbuses[k])
+                        if (a != c) bs.adj[bnode[a]].push_back(bnode[c]);
+            for (auto &v : bs.adj) {
+                std::sort(v.begin(), v.end());
+                v.erase(std::unique(v.begin(), v.end()), v.end());
+            }
+            bsym = build_symbolic(bs);
+            B.F = bsym.F;
+        }
+        B.n_gamma = B.F.n_int;
+        // x_Gamma in oracle order: ascending boundary bus, magnitude then angle
+        std::vector<int> xg0(bbus.size() + 1, 0);
+        for (size_t i = 0; i < bbus.size(); ++i) xg0[i + 1] = xg0[i] + nvar_of(bbus[i]);
+        B.bvar_ibus.assign(B.n_gamma, -1);
+        B.bvar_isT.assign(B.n_gamma, 0);
+        B.xg_of_b.assign(B.n_gamma, -1);
+        for (int p = 0; p < (int)bbus.size(); ++p) {
+            int node = bsym.order[p];
+            int b = bbus[node];
+            int v0 = bsym.var0[p];
+            B.bvar_ibus[v0] = st.ibus_of_bus[b];
+            B.xg_of_b[v0] = xg0[node];
+            if (nvar_of(b) == 2) {
+                B.bvar_ibus[v0 + 1] = st.ibus_of_bus[b];
+                B.bvar_isT[v0 + 1] = 1;
+                B.xg_of_b[v0 + 1] = xg0[node] + 1;
+            }
+        }
+        auto bscalar = [&](int b, int isT) {
+            int p = bsym.pos_of[bnode[b]];
+            return bsym.var0[p] + isT;
+        };
+
+        // ---------------- pass 2: templates and slot maps per area
+        std::vector<int> locpos(N, -1);
+        std::vector<std::vector<int>> asm_lists(B.F.store_total);
+        std::vector<std::vector<std::pair<int, int>>> rhs_lists(B.n_gamma);
+        int zrow = 0;
+        st.zrow_base.assign(K, 0);
+        st.zperm.clear();
+        st.zperm.reserve(st.m);
+        for (int k = 0; k < K; ++k) {
+            AreaSetup &A = st.areas[k];
+            SymResult &sr = sym[k];
+            const std::vector<int> &nd = nodes[k];
+            A.k = k;
+            A.F = sr.F;
+            A.nb_int = (int)nd.size() - (int)lbuses[k].size();
+            A.nb_loc = (int)nd.size();
+            A.n_int = A.F.n_int;
+            A.n_bnd = A.F.n_bnd;
+            A.locbus.resize(A.nb_loc);
+            A.qvarV.resize(A.nb_loc);
+            A.qvarT.resize(A.nb_loc);
+            std::vector<int> bus_at(A.nb_loc);
+            for (int q = 0; q < A.nb_loc; ++q) {
+                int b = nd[sr.order[q]];
+                bus_at[q] = b;
+                locpos[b] = q;
+                A.locbus[q] = st.ibus_of_bus[b];
+                A.qvarV[q] = sr.var0[q];
+                A.qvarT[q] = (sr.var0[q + 1] - sr.var0[q] == 2) ? sr.var0[q] + 1 : -1;
+            }
+            // own buses in internal-numbering order
+            for (int q = 0; q < A.nb_loc; ++q)
+                if (area[bus_at[q]] == k) A.own_q.push_back(q);
+            std::sort(A.own_q.begin(), A.own_q.end(),
+                      [&](int a, int b) { return A.locbus[a] < A.locbus[b]; });
+            A.n_own = (int)A.own_q.size();
+            auto gp = [&](int va, int vb) { return (va < 0 || vb < 0) ? -1 : A.F.pos(va, vb); };
+            const int G = 0;
+            (void)G;
+            for (int o = 0; o < A.n_own; ++o) {
+                int q = A.own_q[o], b = bus_at[q];
+                A.own_ebeg.push_back((int)A.end_qi.size());
+                A.own_sbeg.push_back((int)A.slot_q.size());
+                int pvv = gp(A.qvarV[q], A.qvarV[q]);
+                if (pvv < 0) fail("diagonal slot missing");
+                A.own_gvv.push_back(pvv);
+                std::vector<int> ls = inc[b];
+                std::sort(ls.begin(), ls.end(), [&](int l1, int l2) {
+                    int q1 = locpos[other(l1, b)], q2 = locpos[other(l2, b)];
+                    return q1 != q2 ? q1 < q2 : l1 < l2;
+                });
+                int last_q = -1;
+                for (int l : ls) {
+                    int o2 = other(l, b);
+                    int qj = locpos[o2];
+                    if (qj < 0) fail("neighbour not local");
+                    if (qj != last_q) {
+                        A.slot_q.push_back(qj);
+                        A.slot_ebeg.push_back((int)A.end_qi.size());
+                        A.slot_ecnt.push_back(0);
+                        last_q = qj;
+                    }
+                    ++A.slot_ecnt.back();
+                    A.end_qi.push_back(q);
+                    A.end_qj.push_back(qj);
+                    A.end_own.push_back(o);
+                    int v4[4] = {A.qvarV[q], A.qvarT[q], A.qvarV[qj], A.qvarT[qj]};
+                    for (int a = 0; a < 4; ++a) A.end_var.push_back(v4[a]);
+                    for (int a = 0; a < 4; ++a)
+                        for (int c = a; c < 4; ++c) {
+                            int p = gp(v4[a], v4[c]);
+                            if (v4[a] >= 0 && v4[c] >= 0 && p < 0) fail("flow slot missing");
+                            A.end_gpos.push_back(p);
+                        }
+                    bool is_from = net.from[l] == b;
+                    A.end_canon.push_back(is_from ? 3 * N + l : 3 * N + 2 * L + l);
+                    double den = net.r[l] * net.r[l] + net.x[l] * net.x[l];
+                    A.end_g.push_back(net.r[l] / den);
+                    A.end_b.push_back(-net.x[l] / den);
+                    A.end_bh.push_back(0.5 * net.bc[l]);
+                }
+            }
+            A.n_ends = (int)A.end_qi.size();
+            A.n_slots = (int)A.slot_q.size();
+            A.own_ebeg.push_back(A.n_ends);
+            A.own_sbeg.push_back(A.n_slots);
+            // injection-row gain items over {bus itself, neighbour slots}
+            long long gup = A.n_own;
+            for (int o = 0; o < A.n_own; ++o) {
+                int s0 = A.own_sbeg[o], d = A.own_sbeg[o + 1] - s0;
+                auto slot_bus = [&](int u) { return u == 0 ? A.own_q[o] : A.slot_q[s0 + u - 1]; };
+                for (int u = 0; u <= d; ++u)
+                    for (int v = u; v <= d; ++v) {
+                        int qa = slot_bus(u), qb = slot_bus(v);
+                        int Va = A.qvarV[qa], Ta = A.qvarT[qa], Vb = A.qvarV[qb], Tb = A.qvarT[qb];
+                        int p4[4];
+                        if (u == v) {
+                            p4[0] = gp(Va, Va);
+                            p4[1] = gp(Ta, Va);
+                            p4[2] = gp(Ta, Ta);
+                            p4[3] = -1;
+                        } else {
+                            p4[0] = gp(Va, Vb);
+                            p4[1] = gp(Va, Tb);
+                            p4[2] = gp(Ta, Vb);
+                            p4[3] = gp(Ta, Tb);
+                        }
+                        if (p4[0] < 0) fail("injection slot missing");
+                        A.item_own.push_back(o);
+                        A.item_uv.push_back(u | (v << 16));
+                        for (int a = 0; a < 4; ++a) {
+                            A.item_pos.push_back(p4[a]);
+                            if (p4[a] >= 0) ++gup;
+                        }
+                    }
+            }
+            for (int p : A.end_gpos)
+                if (p >= 0) ++gup;
+            A.n_items = (int)A.item_own.size();
+            A.g_updates = gup;
+            // boundary selector E_k (Eq. Ek_select)
+            A.ebnd.assign(A.n_bnd, -1);
+            A.bnd_xg.assign(A.n_bnd, -1);
+            for (int q = A.nb_int; q < A.nb_loc; ++q) {
+                int b = bus_at[q];
+                int lvV = A.qvarV[q] - A.n_int;
+                A.ebnd[lvV] = bscalar(b, 0);
+                if (A.qvarT[q] >= 0) A.ebnd[lvV + 1] = bscalar(b, 1);
+            }
+            for (int lv = 0; lv < A.n_bnd; ++lv) {
+                if (A.ebnd[lv] < 0) fail("boundary selector incomplete");
+                A.bnd_xg[lv] = B.xg_of_b[A.ebnd[lv]];
+            }
+            // coordinator gather lists (Eq. global_assembly)
+            for (int cb = 0; cb < A.n_bnd; ++cb)
+                for (int rb = cb; rb < A.n_bnd; ++rb) {
+                    int P = B.F.pos(A.ebnd[rb], A.ebnd[cb]);
+                    if (P < 0) fail("boundary slot missing");
+                    asm_lists[P].push_back(k);
+                    asm_lists[P].push_back(A.F.off_B + packed_col_start(cb, A.n_bnd) + (rb - cb));
+                }
+            for (int lv = 0; lv < A.n_bnd; ++lv) rhs_lists[A.ebnd[lv]].push_back({k, lv});
+            // measurement rows of the area (Sec. 4.1 SoA templates)
+            st.zrow_base[k] = zrow;
+            for (int o = 0; o < A.n_own; ++o) st.zperm.push_back(bus_at[A.own_q[o]]);
+            for (int o = 0; o < A.n_own; ++o) st.zperm.push_back(N + bus_at[A.own_q[o]]);
+            for (int o = 0; o < A.n_own; ++o) st.zperm.push_back(2 * N + bus_at[A.own_q[o]]);
+            for (int e = 0; e < A.n_ends; ++e) st.zperm.push_back(A.end_canon[e]);
+            for (int e = 0; e < A.n_ends; ++e) st.zperm.push_back(A.end_canon[e] + L);
+            zrow += 3 * A.n_own + 2 * A.n_ends;
+            A.work = A.F.flops + 40LL * A.n_ends + A.g_updates;
+            for (int q = 0; q < A.nb_loc; ++q) locpos[bus_at[q]] = -1;
+        }
+        if (zrow != st.m || (int)st.zperm.size() != st.m) fail("measurement rows incomplete");
+        {
+            std::vector<char> seen(st.m, 0);
+            for (int r : st.zperm) {
+                if (r < 0 || r >= st.m || seen[r]) fail("measurement row permutation invalid");
+                seen[r] = 1;
+            }
+        }
+        B.asm_beg.assign(B.F.store_total + 1, 0);
+        for (int P = 0; P < B.F.store_total; ++P) {
+            B.asm_beg[P + 1] = B.asm_beg[P] + (int)asm_lists[P].size() / 2;
+            for (size_t i = 0; i < asm_lists[P].size(); i += 2) {
+                B.asm_area.push_back(asm_lists[P][i]);
+                B.asm_off.push_back(asm_lists[P][i + 1]);
+            }
+        }
+        B.rhs_beg.assign(B.n_gamma + 1, 0);
+        for (int g = 0; g < B.n_gamma; ++g) {
+            B.rhs_beg[g + 1] = B.rhs_beg[g] + (int)rhs_lists[g].size();
+            if (rhs_lists[g].empty()) fail("boundary unknown without an area");
+            for (auto &pr : rhs_lists[g]) {
+                B.rhs_area.push_back(pr.first);
+                B.rhs_lv.push_back(pr.second);
+            }
+        }
+    } catch (const std::exception &e) {
+        st.error = e.what();
+        return false;
+    }
+    return true;
+}
+
+}  // namespace mase
+
+// ---------------------------------------------------------------------------
+// Host self-check of the symbolic setup (no GPU): scatter random gain terms
+// through the slot maps exactly as the device accumulation does, check them
+// against a dense assembly, run the supernodal schedule serially and compare
+// the Schur block and the solves with dense Cholesky results.
+// ---------------------------------------------------------------------------
+namespace mase {
+namespace {
+
+struct Rng {
+    unsigned long long s;
+    double next() {   // splitmix64 -> [0, 1)
+        unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+    double sym() { return 2.0 * next() - 1.0; }
+};
+
+// serial emulation of the device schedule (panel + scattered updates)
+void host_factor(const SymFactor &F, std::vector<double> &st, std::vector<double> &y, bool factor) {
+    for (int lev = 0; lev < F.nlev(); ++lev) {
+        for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
+            double *P = st.data() + F.sn_off[s];
+            double *yc = y.data() + F.sn_c0[s];
+            for (int c = 0; c < w; ++c) {
+                double *col = P + (size_t)c * ld;
+                if (factor) {
+                    double d = col[c];
+                    if (!(d > 0)) throw std::runtime_error("selfcheck: non-positive pivot");
+                    d = std::sqrt(d);
+                    for (int r = c + 1; r < ld; ++r) col[r] /= d;
+                    col[c] = d;
+                    for (int c2 = c + 1; c2 < w; ++c2)
+                        for (int r = c2; r < ld; ++r) P[(size_t)c2 * ld + r] -= col[r] * col[c2];
+                }
+                yc[c] /= col[c];
+                for (int r = c + 1; r < w; ++r) yc[r] -= col[r] * yc[c];
+            }
+        }
+        for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
+            const double *Ps = st.data() + F.sn_off[s] + w;
+            const int rb = F.sn_rows[s];
+            if (factor)
+                for (int jr = 0; jr < R; ++jr)
+                    for (int ir = jr; ir < R; ++ir) {
+                        double v = 0;
+                        for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
+                        st[F.colbase[rb + jr] + F.rel[F.relbase[rb + jr] + ir]] -= v;
+                    }
+            for (int ir = 0; ir < R; ++ir) {
+                double v = 0;
+                for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
+                y[F.rows[rb + ir]] -= v;
+            }
+        }
+    }
+}
+
+void host_back(const SymFactor &F, const std::vector<double> &st, std::vector<double> &y) {
+    for (int lev = F.nlev() - 1; lev >= 0; --lev)
+        for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R, c0 = F.sn_c0[s];
+            const double *P = st.data() + F.sn_off[s];
+            for (int c = 0; c < w; ++c)
+                for (int ir = 0; ir < R; ++ir) y[c0 + c] -= P[(size_t)c * ld + w + ir] * y[F.rows[F.sn_rows[s] + ir]];
+            for (int c = w - 1; c >= 0; --c) {
+                for (int r = c + 1; r < w; ++r) y[c0 + c] -= P[(size_t)c * ld + r] * y[c0 + r];
+                y[c0 + c] /= P[(size_t)c * ld + c];
+            }
+        }
+}
+
+// dense Cholesky in place (lower, row-major n x n); returns false if not SPD
+bool dense_chol(std::vector<double> &A, int n) {
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0)) return false;
+        d = std::sqrt(d);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = v / d;
+        }
+    }
+    return true;
+}
+void dense_solve(const std::vector<double> &Lc, int n, std::vector<double> &b) {
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < i; ++k) b[i] -= Lc[(size_t)i * n + k] * b[k];
+        b[i] /= Lc[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int k = i + 1; k < n; ++k) b[i] -= Lc[(size_t)k * n + i] * b[k];
+        b[i] /= Lc[(size_t)i * n + i];
+    }
+}
+
+double rel_err(const std::vector<double> &a, const std::vector<double> &b) {
+    double num = 0, den = 0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        num = std::max(num, std::fabs(a[i] - b[i]));
+        den = std::max(den, std::fabs(b[i]));
+    }
+    return den > 0 ? num / den : num;
+}
+
+// factor a dense SPD matrix given in full (nv x nv) through symbolic factor F;
+// returns max relative errors of (Schur block, full solve)
+void check_system(const SymFactor &F, const std::vector<double> &Gd, const std::vector<double> &st0,
+                  Rng &rng, double &e_schur, double &e_solve) {
+    const int ni = F.n_int, nb = F.n_bnd, nv = ni + nb;
+    std::vector<double> st = st0, y(nv, 0.0);
+    host_factor(F, st, y, true);
+    // dense Schur: S = G_bb - G_bi G_ii^{-1} G_ib
+    std::vector<double> Gii((size_t)ni * ni);
+    for (int i = 0; i < ni; ++i)
+        for (int j = 0; j < ni; ++j) Gii[(size_t)i * ni + j] = Gd[(size_t)i * nv + j];
+    if (!dense_chol(Gii, ni)) throw std::runtime_error("selfcheck: dense G_ii not SPD");
+    if (nb) {
+        std::vector<double> Sd((size_t)nb * nb), Sg((size_t)nb * nb);
+        for (int c = 0; c < nb; ++c) {
+            std::vector<double> col(ni);
+            for (int i = 0; i < ni; ++i) col[i] = Gd[(size_t)i * nv + ni + c];
+            if (ni) dense_solve(Gii, ni, col);
+            for (int r = 0; r < nb; ++r) {
+                double v = Gd[(size_t)(ni + r) * nv + ni + c];
+                for (int i = 0; i < ni; ++i) v -= Gd[(size_t)(ni + r) * nv + i] * col[i];
+                Sd[(size_t)r * nb + c] = v;
+            }
+        }
+        for (int c = 0; c < nb; ++c)
+            for (int r = 0; r < nb; ++r) {
+                int rr = std::max(r, c), cc = std::min(r, c);
+                Sg[(size_t)r * nb + c] = st[F.pos(ni + rr, ni + cc)];
+            }
+        e_schur = std::max(e_schur, rel_err(Sg, Sd));
+    }
+    // full solve with a random rhs: internal elimination, then the boundary part densely
+    std::vector<double> b(nv);
+    for (auto &v : b) v = rng.sym();
+    std::vector<double> yy = b;
+    std::vector<double> st2 = st0;
+    host_factor(F, st2, yy, true);
+    if (nb) {
+        std::vector<double> Sb((size_t)nb * nb);
+        for (int r = 0; r < nb; ++r)
+            for (int c = 0; c < nb; ++c) Sb[(size_t)r * nb + c] = st2[F.pos(ni + std::max(r, c), ni + std::min(r, c))];
+        if (!dense_chol(Sb, nb)) throw std::runtime_error("selfcheck: Schur block not SPD");
+        std::vector<double> xb(yy.begin() + ni, yy.end());
+        dense_solve(Sb, nb, xb);
+        for (int r = 0; r < nb; ++r) yy[ni + r] = xb[r];
+    }
+    host_back(F, st2, yy);
+    std::vector<double> Gfull = Gd;
+    if (!dense_chol(Gfull, nv)) throw std::runtime_error("selfcheck: dense G not SPD");
+    std::vector<double> xd = b;
+    dense_solve(Gfull, nv, xd);
+    e_solve = std::max(e_solve, rel_err(yy, xd));
+}
+
+}  // namespace
+
+bool selfcheck(const Setup &S, unsigned long long seed, double out[4], std::string &err) {
+    try {
+        Rng rng{seed};
+        double e_slot = 0, e_schur = 0, e_solve = 0, e_bnd = 0;
+        for (const AreaSetup &A : S.areas) {
+            const SymFactor &F = A.F;
+            const int nv = F.n_int + F.n_bnd;
+            std::vector<double> Gd((size_t)nv * nv, 0.0), st(F.store_total, 0.0);
+            auto addd = [&](int a, int b, double v) {
+                if (a < 0 || b < 0) return;
+                Gd[(size_t)a * nv + b] += v;
+                if (a != b) Gd[(size_t)b * nv + a] += v;
+            };
+            // voltage rows
+            for (int o = 0; o < A.n_own; ++o) {
+                double w = 0.5 + rng.next();
+                st[A.own_gvv[o]] += w;
+                addd(A.qvarV[A.own_q[o]], A.qvarV[A.own_q[o]], w);
+            }
+            std::vector<double> dPe(4 * A.n_ends), dQe(4 * A.n_ends);
+            for (int e = 0; e < A.n_ends; ++e) {
+                double dP[4], dQ[4];
+                for (int a = 0; a < 4; ++a) {
+                    dP[a] = rng.sym();
+                    dQ[a] = rng.sym();
+                    dPe[4 * e + a] = dP[a];
+                    dQe[4 * e + a] = dQ[a];
+                }
+                double wp = 0.5 + rng.next(), wq = 0.5 + rng.next();
+                const int *v = &A.end_var[4 * e];
+                int idx = 0;
+                for (int a = 0; a < 4; ++a)
+                    for (int c = a; c < 4; ++c, ++idx) {
+                        double val = wp * dP[a] * dP[c] + wq * dQ[a] * dQ[c];
+                        int p = A.end_gpos[10 * e + idx];
+                        if (p >= 0) st[p] += val;
+                        if (v[a] >= 0 && v[c] >= 0) addd(std::max(v[a], v[c]), std::min(v[a], v[c]), val);
+                    }
+            }
+            // injection rows: h = self part + neighbour parts of the bus's ends
+            std::vector<double> wP(A.n_own), wQ(A.n_own);
+            for (int o = 0; o < A.n_own; ++o) {
+                wP[o] = 0.5 + rng.next();
+                wQ[o] = 0.5 + rng.next();
+                std::vector<double> hP(nv, 0.0), hQ(nv, 0.0);
+                for (int e = A.own_ebeg[o]; e < A.own_ebeg[o + 1]; ++e) {
+                    const int *v = &A.end_var[4 * e];
+                    for (int a = 0; a < 4; ++a)
+                        if (v[a] >= 0) {
+                            hP[v[a]] += dPe[4 * e + a];
+                            hQ[v[a]] += dQe[4 * e + a];
+                        }
+                }
+                for (int a = 0; a < nv; ++a)
+                    if (hP[a] != 0 || hQ[a] != 0)
+                        for (int b = 0; b <= a; ++b) {
+                            double val = wP[o] * hP[a] * hP[b] + wQ[o] * hQ[a] * hQ[b];
+                            if (val != 0) addd(a, b, val);
+                        }
+            }
+            for (int it = 0; it < A.n_items; ++it) {
+                const int o = A.item_own[it], u = A.item_uv[it] & 0xffff, v = A.item_uv[it] >> 16;
+                const int sb = A.own_sbeg[o];
+                double pu[4], pv[4];
+                for (int t = 0; t < 2; ++t) {
+                    int sl = t == 0 ? u : v;
+                    double *dst = t == 0 ? pu : pv;
+                    for (int a = 0; a < 4; ++a) dst[a] = 0;
+                    if (sl == 0) {
+                        for (int e = A.own_ebeg[o]; e < A.own_ebeg[o + 1]; ++e) {
+                            dst[0] += dPe[4 * e + 0];
+                            dst[1] += dPe[4 * e + 1];
+                            dst[2] += dQe[4 * e + 0];
+                            dst[3] += dQe[4 * e + 1];
+                        }
+                    } else {
+                        int ss = sb + sl - 1;
+                        for (int e = A.slot_ebeg[ss]; e < A.slot_ebeg[ss] + A.slot_ecnt[ss]; ++e) {
+                            dst[0] += dPe[4 * e + 2];
+                            dst[1] += dPe[4 * e + 3];
+                            dst[2] += dQe[4 * e + 2];
+                            dst[3] += dQe[4 * e + 3];
+                        }
+                    }
+                }
+                const int *p4 = &A.item_pos[4 * it];
+                double wp = wP[o], wq = wQ[o];
+                if (u == v) {
+                    st[p4[0]] += wp * pu[0] * pu[0] + wq * pu[2] * pu[2];
+                    if (p4[1] >= 0) st[p4[1]] += wp * pu[1] * pu[0] + wq * pu[3] * pu[2];
+                    if (p4[2] >= 0) st[p4[2]] += wp * pu[1] * pu[1] + wq * pu[3] * pu[3];
+                } else {
+                    st[p4[0]] += wp * pu[0] * pv[0] + wq * pu[2] * pv[2];
+                    if (p4[1] >= 0) st[p4[1]] += wp * pu[0] * pv[1] + wq * pu[2] * pv[3];
+                    if (p4[2] >= 0) st[p4[2]] += wp * pu[1] * pv[0] + wq * pu[3] * pv[2];
+                    if (p4[3] >= 0) st[p4[3]] += wp * pu[1] * pv[1] + wq * pu[3] * pv[3];
+                }
+            }
+            // every dense entry must sit at its storage slot with the same value
+            double scale = 0;
+            for (double v : Gd) scale = std::max(scale, std::fabs(v));
+            for (int c = 0; c < nv; ++c)
+                for (int r = c; r < nv; ++r) {
+                    double d = Gd[(size_t)r * nv + c];
+                    int p = F.pos(r, c);
+                    if (p < 0) {
+                        if (d != 0) throw std::runtime_error("selfcheck: gain entry outside the pattern");
+                        continue;
+                    }
+                    e_slot = std::max(e_slot, std::fabs(st[p] - d) / scale);
+                }
+            // make it comfortably SPD (diagonal shift) in both copies
+            for (int i = 0; i < nv; ++i) {
+                Gd[(size_t)i * nv + i] += 4.0 * scale;
+                st[F.pos(i, i)] += 4.0 * scale;
+            }
+            check_system(F, Gd, st, rng, e_schur, e_solve);
+        }
+        // boundary system: random SPD blocks per area scattered through the gather lists
+        const BoundarySetup &B = S.B;
+        if (B.n_gamma > 0) {
+            const int nG = B.n_gamma;
+            std::vector<std::vector<double>> Sk(S.areas.size());
+            for (size_t k = 0; k < S.areas.size(); ++k) {
+                const AreaSetup &A = S.areas[k];
+                Sk[k].assign(A.F.store_total, 0.0);
+                for (int c = 0; c < A.n_bnd; ++c)
+                    for (int r = c; r < A.n_bnd; ++r)
+                        Sk[k][A.F.pos(A.n_int + r, A.n_int + c)] = rng.sym() + (r == c ? 2.0 * A.n_bnd : 0.0);
+            }
+            std::vector<double> st(B.F.store_total, 0.0), Sd((size_t)nG * nG, 0.0);
+            for (int P = 0; P < B.F.store_total; ++P)
+                for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i) st[P] += Sk[B.asm_area[i]][B.asm_off[i]];
+            for (size_t k = 0; k < S.areas.size(); ++k) {
+                const AreaSetup &A = S.areas[k];
+                for (int c = 0; c < A.n_bnd; ++c)
+                    for (int r = c; r < A.n_bnd; ++r) {
+                        double v = Sk[k][A.F.pos(A.n_int + r, A.n_int + c)];
+                        int gr = A.ebnd[r], gc = A.ebnd[c];
+                        Sd[(size_t)gr * nG + gc] += v;
+                        if (gr != gc) Sd[(size_t)gc * nG + gr] += v;
+                    }
+            }
+            double sb = 0, dummy = 0;
+            check_system(B.F, Sd, st, rng, dummy, sb);
+            e_bnd = sb;
+        }
+        out[0] = e_slot;
+        out[1] = e_schur;
+        out[2] = e_solve;
+        out[3] = e_bnd;
+    } catch (const std::exception &e) {
+        err = e.what();
+        return false;
+    }
+    return true;
+}
+
+}  // namespace mase

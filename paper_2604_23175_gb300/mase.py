@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libmase (argument marshalling only).
+
+Every compute step runs in the CUDA library; this module converts NumPy
+arrays or CUDA tensors to pointers and back.  Loading fails loudly when the
+library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmase.so")
+
+MASE_OK, MASE_NOT_CONVERGED = 0, 1
+MASE_EINVAL, MASE_EUNOBSERVABLE, MASE_ENONFINITE, MASE_EDEVICE, MASE_ENOTREADY = -1, -2, -3, -4, -5
+SNAP_CONVERGED, SNAP_MAX_ITER, SNAP_NOT_SPD, SNAP_NONFINITE = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+START_FLAT, START_X0, START_LEARNED = 0, 1, 2
+PER_AREA, BATCHED = 0, 1
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_u8p = C.POINTER(C.c_uint8)
+
+
+class Network(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("slack_bus", C.c_int32),
+                ("from_bus", _i32p), ("to_bus", _i32p), ("r", _f64p), ("x", _f64p),
+                ("b_charge", _f64p)]
+
+
+class Partition(C.Structure):
+    _fields_ = [("n_area", C.c_int32), ("area_of_bus", _i32p)]
+
+
+class Measurements(C.Structure):
+    _fields_ = [("n_snap", C.c_int32), ("z", C.c_void_p), ("sigma", _f64p), ("mask", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
+                ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", _i32p), ("status", _i32p), ("J", _f64p), ("max_step", _f64p),
+                ("stage_ms", C.c_double * 4), ("total_launches", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_area", C.c_int32),
+                ("n_snap", C.c_int32), ("n_meas", C.c_int32), ("n_state", C.c_int32),
+                ("n_boundary_bus", C.c_int32), ("n_gamma", C.c_int32),
+                ("max_area_vars", C.c_int32), ("max_area_nb", C.c_int32),
+                ("factor_nnz", C.c_int64), ("local_flops", C.c_int64),
+                ("boundary_flops", C.c_int64), ("g_updates", C.c_int64),
+                ("smem_bytes_max", C.c_int32), ("areas_in_smem", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+class MaseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{code} ({status_str(code)}): {msg}")
+        self.code = code
+
+
+def load() -> C.CDLL:
+    """Load libmase.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmase.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    H = C.c_void_p
+    sig = {
+        "mase_default_options": (None, [C.POINTER(Options)]),
+        "mase_create": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.POINTER(Measurements),
+                                  C.POINTER(Options), C.POINTER(H)]),
+        "mase_set_measurements": (C.c_int, [H, C.POINTER(Measurements)]),
+        "mase_solve": (C.c_int, [H, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.POINTER(Stats)]),
+        "mase_measure": (C.c_int, [H, C.c_void_p, C.c_int32, C.c_void_p]),
+        "mase_get_info": (C.c_int, [H, C.POINTER(Info)]),
+        "mase_set_start_mode": (C.c_int, [H, C.c_int32]),
+        "mase_destroy": (None, [H]),
+        "mase_status_str": (C.c_char_p, [C.c_int]),
+        "mase_last_error": (C.c_char_p, []),
+        "mase_analyze": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.POINTER(Info)]),
+        "mase_selfcheck": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.c_uint64, _f64p]),
+        "mase_analyze_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    return load().mase_status_str(code).decode()
+
+
+def _last_error() -> str:
+    return load().mase_last_error().decode()
+
+
+def _ptr(a, ctype=None):
+    """Pointer of a NumPy array or a torch CUDA/CPU tensor (contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class _Keep:
+    """Host arrays referenced by ctypes structs (kept alive by the caller)."""
+    arrays: list
+
+
+def _network(grid):
+    fr = np.ascontiguousarray(grid.from_bus, dtype=np.int32)
+    to = np.ascontiguousarray(grid.to_bus, dtype=np.int32)
+    r = np.ascontiguousarray(grid.r, dtype=np.float64)
+    x = np.ascontiguousarray(grid.x, dtype=np.float64)
+    b = np.ascontiguousarray(grid.b_charge, dtype=np.float64)
+    ar = np.ascontiguousarray(grid.area_of_bus, dtype=np.int32)
+    net = Network(int(grid.n_bus), int(len(fr)), int(grid.slack),
+                  fr.ctypes.data_as(_i32p), to.ctypes.data_as(_i32p), r.ctypes.data_as(_f64p),
+                  x.ctypes.data_as(_f64p), b.ctypes.data_as(_f64p))
+    part = Partition(int(grid.n_area), ar.ctypes.data_as(_i32p))
+    return net, part, _Keep([fr, to, r, x, b, ar])
+
+
+def analyze(grid) -> dict:
+    """Host-only structural analysis of the setup (no GPU needed)."""
+    lib = load()
+    net, part, keep = _network(grid)
+    info = Info()
+    rc = lib.mase_analyze(C.byref(net), C.byref(part), C.byref(info))
+    if rc != MASE_OK:
+        raise MaseError(rc, lib.mase_analyze_error().decode())
+    del keep
+    return info.as_dict()
+
+
+def selfcheck(grid, seed: int = 1) -> np.ndarray:
+    """Host-only check of the symbolic setup against dense Cholesky (no GPU)."""
+    lib = load()
+    net, part, keep = _network(grid)
+    out = np.zeros(4)
+    rc = lib.mase_selfcheck(C.byref(net), C.byref(part), seed, out.ctypes.data_as(_f64p))
+    if rc != MASE_OK:
+        raise MaseError(rc, lib.mase_analyze_error().decode())
+    del keep
+    return out
+
+
+def default_options() -> Options:
+    o = Options()
+    load().mase_default_options(C.byref(o))
+    return o
+
+
+@dataclass
+class SolveResult:
+    rc: int
+    iters: np.ndarray
+    status: np.ndarray
+    J: np.ndarray
+    max_step: np.ndarray
+    launches: int
+
+
+class Estimator:
+    """One handle: a network, its partition and a batch of n_snap snapshots."""
+
+    def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
+                 schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None):
+        self.lib = load()
+        net, part, keep = _network(grid)
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        opt = default_options()
+        opt.precision, opt.schedule, opt.use_graph = precision, schedule, int(bool(use_graph))
+        opt.refine, opt.threads, opt.device = refine, threads, device
+        opt.stream = C.c_void_p(stream) if stream else None
+        meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
+        h = C.c_void_p()
+        rc = self.lib.mase_create(C.byref(net), C.byref(part), C.byref(meas), C.byref(opt), C.byref(h))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+        self.h = h
+        self.n_snap = int(n_snap)
+        self.n_bus = int(grid.n_bus)
+        self.n_meas = int(grid.n_meas)
+        del keep
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mase_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_measurements(self, z, mask=None):
+        meas = Measurements(self.n_snap, _ptr(z), None, _ptr(mask))
+        rc = self.lib.mase_set_measurements(self.h, C.byref(meas))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def set_start_mode(self, mode: int):
+        rc = self.lib.mase_set_start_mode(self.h, mode)
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def solve(self, x0=None, tol=1e-8, max_iter=10, x_out=None, check=True) -> SolveResult:
+        """Solve the batch.  x_out: host array or CUDA tensor [n_snap, 2N]."""
+        S = self.n_snap
+        iters = np.zeros(S, dtype=np.int32)
+        status = np.zeros(S, dtype=np.int32)
+        J = np.zeros(S)
+        ms = np.zeros(S)
+        st = Stats(iters.ctypes.data_as(_i32p), status.ctypes.data_as(_i32p),
+                   J.ctypes.data_as(_f64p), ms.ctypes.data_as(_f64p))
+        rc = self.lib.mase_solve(self.h, _ptr(x0), float(tol), int(max_iter), _ptr(x_out), C.byref(st))
+        if check and rc < 0:
+            raise MaseError(rc, _last_error())
+        return SolveResult(rc, iters, status, J, ms, int(st.total_launches))
+
+    def measure(self, x, z_out, n_snap=None):
+        n = self.n_snap if n_snap is None else n_snap
+        rc = self.lib.mase_measure(self.h, _ptr(x), int(n), _ptr(z_out))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def info(self) -> dict:
+        inf = Info()
+        rc = self.lib.mase_get_info(self.h, C.byref(inf))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+        return inf.as_dict()

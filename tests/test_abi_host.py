@@ -1,0 +1,102 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol,
+and its host-side symbolic setup matches the oracle's partition and dense
+Cholesky (no GPU calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import wls
+from paper_2604_23175_gb300 import synth
+from tests.helpers import net_of, tiny_grid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mase():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2604_23175_gb300 import mase as m
+    m.load()
+    return m
+
+
+def _declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(mase_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(mase):
+    import ctypes
+    lib = ctypes.CDLL(mase.LIB_PATH)
+    names = _declared_functions()
+    assert "mase_create" in names and "mase_solve" in names and "mase_destroy" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_defaults(mase):
+    assert mase.status_str(0) == "MASE_OK"
+    assert mase.status_str(-2) == "MASE_EUNOBSERVABLE"
+    o = mase.default_options()
+    assert o.precision == mase.MIXED and o.schedule == mase.BATCHED and o.refine == 1
+
+
+@pytest.mark.parametrize("name", ["grid300_k4", "grid2869_k16", "grid9241_k32"])
+def test_setup_counts_match_oracle_partition(mase, name):
+    g = synth.make_grid(name)
+    info = mase.analyze(g)
+    part = wls.partition(net_of(g), g.area_of_bus, g.n_area)
+    assert info["n_state"] == 2 * g.n_bus - 1
+    assert info["n_meas"] == 3 * g.n_bus + 4 * g.n_branch
+    assert info["n_boundary_bus"] == len(part.boundary_buses)
+    assert info["n_gamma"] == len(part.gamma_cols)
+    nb = max(len(c) for c in part.boundary_cols)
+    assert info["max_area_nb"] == nb
+
+
+@pytest.mark.parametrize("name,slack_b", [("grid300_k4", False), ("grid2869_k16", False),
+                                           ("grid2869_k16", True)])
+def test_symbolic_setup_selfcheck(mase, name, slack_b):
+    g = synth.make_grid(name, slack_on_boundary=slack_b)
+    err = mase.selfcheck(g, seed=7)
+    assert np.all(err < 1e-12), err
+
+
+def test_selfcheck_tiny_and_single_area(mase):
+    g = tiny_grid(12, 3, seed=5)
+    assert np.all(mase.selfcheck(g, 1) < 1e-12)
+    g1 = tiny_grid(10, 1, seed=2)
+    info = mase.analyze(g1)
+    assert info["n_gamma"] == 0
+    assert np.all(mase.selfcheck(g1, 1) < 1e-12)
+
+
+def test_invalid_inputs_rejected_on_host(mase):
+    g = synth.make_grid("grid300_k4")
+    bad = synth.Grid(g.n_bus, g.from_bus.copy(), g.to_bus.copy(), g.r, g.x, g.b_charge,
+                     g.area_of_bus, g.n_area, 0)
+    bad.to_bus[3] = bad.from_bus[3]
+    with pytest.raises(mase.MaseError) as e:
+        mase.analyze(bad)
+    assert e.value.code == mase.MASE_EINVAL
+    bad2 = synth.Grid(g.n_bus, g.from_bus, g.to_bus, g.r, g.x, g.b_charge,
+                      g.area_of_bus.copy(), g.n_area, 0)
+    bad2.area_of_bus[0] = 99
+    with pytest.raises(mase.MaseError):
+        mase.analyze(bad2)
+    bad3 = synth.Grid(g.n_bus, g.from_bus.copy(), g.to_bus, g.r, g.x, g.b_charge,
+                      g.area_of_bus, g.n_area, 0)
+    bad3.from_bus[0] = g.n_bus
+    with pytest.raises(mase.MaseError):
+        mase.analyze(bad3)

@@ -1,0 +1,205 @@
+"""GPU parity of libmase against the FP64 CPU oracle, through the C ABI.
+
+Bars (from the method's stated accuracy targets): converged state within
+1e-6 in |dV| and |dtheta| and J = r^T W r within 1e-8 relative of the oracle's
+converged WLS estimate; the FP64 path additionally takes the oracle's
+iteration counts (a condensed step equals the centralised step).
+"""
+import numpy as np
+import pytest
+
+from oracle import wls
+from paper_2604_23175_gb300 import synth
+from tests.helpers import net_of, problem
+
+pytestmark = pytest.mark.gpu
+
+STATE_TOL = 1e-6
+J_RTOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def mase():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2604_23175_gb300 import mase as m
+    m.load()
+    return m
+
+
+def _run(mase, grid, sig, z, mask=None, precision=None, schedule=None, x0=None, tol=1e-8,
+         max_iter=20, **kw):
+    S = z.shape[0]
+    est = mase.Estimator(grid, sig, S, z=z, mask=mask, precision=precision, schedule=schedule, **kw)
+    x = np.zeros((S, 2 * grid.n_bus))
+    res = est.solve(x0=x0, tol=tol, max_iter=max_iter, x_out=x, check=False)
+    est.close()
+    return x, res
+
+
+def _check(net, grid, x, res, z, w, snaps, tol=1e-8, same_iters=False, x0=None):
+    N = grid.n_bus
+    for s in snaps:
+        v0 = (None, None) if x0 is None else (x0[s, :N], x0[s, N:])
+        ref = wls.gauss_newton(net, z[s], w if w.ndim == 1 else w[s], Vm0=v0[0], Va0=v0[1],
+                               tol=tol, max_iter=30)
+        assert ref.converged
+        dV = np.max(np.abs(x[s, :N] - ref.Vm))
+        dT = np.max(np.abs(x[s, N:] - ref.Va))
+        assert dV <= STATE_TOL and dT <= STATE_TOL, (s, dV, dT)
+        assert abs(res.J[s] - ref.J) <= J_RTOL * ref.J, (s, res.J[s], ref.J)
+        assert res.status[s] == 0
+        if same_iters:
+            assert res.iters[s] == ref.iters, (s, res.iters[s], ref.iters)
+
+
+def test_measure_matches_oracle(mase):
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 3, 3100)
+    est = mase.Estimator(g, sig, 3, z=z)
+    x = np.concatenate([Vm, Va], axis=1)
+    out = np.zeros_like(z)
+    est.measure(np.ascontiguousarray(x), out)
+    est.close()
+    for s in range(3):
+        h = wls.measure(net, Vm[s], Va[s])
+        assert np.max(np.abs(out[s] - h)) <= 1e-11 * max(1.0, np.max(np.abs(h)))
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("schedule", ["PER_AREA", "BATCHED"])
+@pytest.mark.parametrize("name", ["grid300_k4", "grid2869_k16"])
+def test_parity_small_grids(mase, name, precision, schedule):
+    g = synth.make_grid(name)
+    net, Vm, Va, z, sig = problem(g, 2, 3200)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=getattr(mase, precision),
+                  schedule=getattr(mase, schedule))
+    assert res.rc == mase.MASE_OK, res
+    _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
+
+
+def test_parity_slack_on_boundary(mase):
+    g = synth.make_grid("grid2869_k16", slack_on_boundary=True)
+    net, Vm, Va, z, sig = problem(g, 2, 3300)
+    w = wls.weights(sig)
+    for prec in (mase.FP64, mase.MIXED):
+        x, res = _run(mase, g, sig, z, precision=prec, schedule=mase.BATCHED)
+        assert res.rc == mase.MASE_OK
+        _check(net, g, x, res, z, w, range(2), same_iters=(prec == mase.FP64))
+        assert np.all(x[:, g.n_bus + g.slack] == 0.0)
+
+
+def test_parity_random_row_drops(mase):
+    g = synth.make_grid("grid2869_k16")
+    S = 4
+    net, Vm, Va, z, sig = problem(g, S, 3400)
+    mask = synth.make_mask(g, S, 0.10, 3401)
+    W = np.stack([wls.weights(sig, mask[s]) for s in range(S)])
+    for prec in (mase.FP64, mase.MIXED):
+        x, res = _run(mase, g, sig, z, mask=mask, precision=prec, schedule=mase.BATCHED)
+        assert res.rc == mase.MASE_OK
+        _check(net, g, x, res, z, W, range(S), same_iters=(prec == mase.FP64))
+
+
+def test_parity_family_mask(mase):
+    """Structured masking of a whole flow family (Sec. 5.4 experiment)."""
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 1, 3450)
+    for fam in ("Pf", "Qt"):
+        mask = synth.family_mask(g, fam, 1)
+        w = wls.weights(sig, mask[0])
+        x, res = _run(mase, g, sig, z, mask=mask, precision=mase.MIXED, schedule=mase.BATCHED)
+        assert res.rc == mase.MASE_OK
+        _check(net, g, x, res, z, w, [0])
+
+
+@pytest.mark.parametrize("precision,schedule", [("MIXED", "BATCHED"), ("FP64", "PER_AREA")])
+def test_parity_9241_bus_64_snapshots_sampled(mase, precision, schedule):
+    """The benchmark workload (9241-bus shape, 32 areas, 64-step random walk)
+    in the launch configuration the benchmark times; the oracle checks a sample."""
+    g = synth.make_grid("grid9241_k32")
+    net, Vm, Va, z, sig = problem(g, 64, 2002)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=getattr(mase, precision),
+                  schedule=getattr(mase, schedule), max_iter=10)
+    assert res.rc == mase.MASE_OK, (res.rc, res.status)
+    assert np.all(res.status == 0)
+    _check(net, g, x, res, z, w, [0, 37, 63], same_iters=(precision == "FP64"))
+
+
+def test_start_from_solution_takes_one_step(mase):
+    g = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(g, 2, 3500)
+    w = wls.weights(sig)
+    x0 = np.zeros((2, 2 * g.n_bus))
+    for s in range(2):
+        ref = wls.gauss_newton(net, z[s], w, tol=1e-13, max_iter=30)
+        x0[s] = np.concatenate([ref.Vm, ref.Va])
+    x, res = _run(mase, g, sig, z, x0=x0, precision=mase.MIXED, schedule=mase.BATCHED)
+    assert res.rc == mase.MASE_OK
+    assert np.all(res.iters == 1)
+    assert np.max(np.abs(x - x0)) < 1e-8
+
+
+def test_device_pointers_match_host(mase):
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 3, 3600)
+    xh, rh = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED)
+    zd = torch.tensor(z, device="cuda")
+    est = mase.Estimator(g, sig, 3, z=zd, precision=mase.MIXED, schedule=mase.BATCHED)
+    xd = torch.zeros((3, 2 * g.n_bus), dtype=torch.float64, device="cuda")
+    rd = est.solve(tol=1e-8, max_iter=20, x_out=xd)
+    est.close()
+    assert np.array_equal(rd.iters, rh.iters)
+    assert np.max(np.abs(xd.cpu().numpy() - xh)) < 1e-9
+
+
+def test_unobservable_snapshot_reports_status(mase):
+    g = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(g, 2, 3700)
+    mask = np.ones((2, g.n_meas), dtype=np.uint8)
+    mask[1, :] = 0                       # snapshot 1 has no measurements at all
+    x, res = _run(mase, g, sig, z, mask=mask, precision=mase.MIXED, schedule=mase.BATCHED)
+    assert res.rc == mase.MASE_EUNOBSERVABLE
+    assert res.status[0] == mase.SNAP_CONVERGED
+    assert res.status[1] == mase.SNAP_NOT_SPD
+
+
+def test_nonfinite_measurement_reports_status(mase):
+    g = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(g, 2, 3800)
+    z = z.copy()
+    z[1, 5] = np.nan
+    x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED)
+    assert res.status[0] == mase.SNAP_CONVERGED
+    assert res.status[1] == mase.SNAP_NONFINITE
+    assert res.rc == mase.MASE_ENONFINITE
+
+
+def test_max_iter_reports_not_converged(mase):
+    g = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(g, 1, 3900)
+    x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED, max_iter=1)
+    assert res.rc == mase.MASE_NOT_CONVERGED
+    assert res.status[0] == mase.SNAP_MAX_ITER and res.iters[0] == 1
+
+
+def test_repeat_solves_and_launch_counts(mase):
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 2, 4000)
+    est = mase.Estimator(g, sig, 2, z=z, precision=mase.MIXED, schedule=mase.BATCHED)
+    x1 = np.zeros((2, 2 * g.n_bus))
+    x2 = np.zeros_like(x1)
+    r1 = est.solve(tol=1e-8, max_iter=20, x_out=x1)
+    r2 = est.solve(tol=1e-8, max_iter=20, x_out=x2)
+    est.close()
+    assert np.array_equal(r1.iters, r2.iters)
+    assert np.max(np.abs(x1 - x2)) < 1e-10
+    it = int(r1.iters.max())
+    # reset + state-in + 4 per step (local, boundary, back, bookkeeping) + objective + state-out
+    assert r1.launches == 2 + 4 * it + 2
