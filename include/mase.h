@@ -111,6 +111,8 @@ typedef struct {
     int32_t threads;     /* threads per CTA of the area kernels, 0=auto */
     int32_t device;      /* CUDA device ordinal                         */
     void   *stream;      /* cudaStream_t, NULL = default stream         */
+    int32_t profile;     /* 1: time each stage with CUDA events into
+                            mase_stats.stage_ms                          */
 } mase_options;
 
 /* Per-solve results.  Arrays are host arrays of n_snap entries supplied by
@@ -120,9 +122,12 @@ typedef struct {
     int32_t *status;      /* MASE_SNAP_* per snapshot                           */
     double  *J;           /* r^T W r at the returned state, per snapshot        */
     double  *max_step;    /* max |dx| of the last step, per snapshot            */
-    double   stage_ms[4]; /* device time: local / boundary / back-substitution /
-                             other, summed over the solve (0 unless profiling)  */
+    double   stage_ms[4]; /* device time of the area kernel (evaluation, accumulation,
+                             condensation), the coordinator, the back-substitution
+                             and the bookkeeping, summed over the solve's steps
+                             (0 unless options.profile)                          */
     int32_t  total_launches; /* kernels launched by the solve                   */
+    int32_t  steps;          /* Gauss-Newton steps run for the batch (max over snapshots) */
 } mase_stats;
 
 /* Structural sizes of a handle (host-side setup results). */

@@ -156,6 +156,7 @@ struct mase_handle {
     DevBuf<StopRule> stop;
     cudaStream_t user_stream = nullptr;   // caller's stream (NULL = legacy default stream)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_stage[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     mase_info info{};
 
     ~mase_handle() {
@@ -164,6 +165,8 @@ struct mase_handle {
         if (h_n_active) cudaFreeHost(h_n_active);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        for (auto &e : ev_stage)
+            if (e) cudaEventDestroy(e);
         if (stream) cudaStreamDestroy(stream);
     }
 };
@@ -211,6 +214,12 @@ State make_state(mase_handle *h) {
 
 // One Gauss-Newton step for every active snapshot: local condensation,
 // coordinator, back-substitution, bookkeeping.
+// Stage boundaries are recorded as external event nodes so that they also
+// time the replays of a captured graph.
+inline void mark(mase_handle *h, int i) {
+    if (h->opt.profile) cudaEventRecordWithFlags(h->ev_stage[i], h->stream, cudaEventRecordExternal);
+}
+
 template <class RG, class RS>
 int enqueue_step(mase_handle *h, int *launches) {
     State X = make_state(h);
@@ -218,6 +227,7 @@ int enqueue_step(mase_handle *h, int *launches) {
     const int S = h->n_snap, K = h->S.K, nt = h->threads;
     RG *fac = (RG *)h->fac.p;
     RS *cv = (RS *)h->cvec.p;
+    mark(h, 0);
     if (h->opt.schedule == MASE_BATCHED) {
         k_local<RG, RS><<<K * S, nt, h->smem_local, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1,
                                                          MODE_FULL, fac, cv, h->bh.p);
@@ -229,12 +239,14 @@ int enqueue_step(mase_handle *h, int *launches) {
             ++*launches;
         }
     }
+    mark(h, 1);
     if (h->bnd.n_gamma > 0) {
         k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
                                                       (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p,
                                                       h->opt.precision == MASE_MIXED ? h->opt.refine : 0);
         ++*launches;
     }
+    mark(h, 2);
     if (h->opt.schedule == MASE_BATCHED) {
         k_back<RG, RS><<<K * S, nt, h->smem_back, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1, fac,
                                                        cv, h->dxG.p, h->bnd.n_gamma);
@@ -247,6 +259,7 @@ int enqueue_step(mase_handle *h, int *launches) {
             ++*launches;
         }
     }
+    mark(h, 3);
     return MASE_OK;
 }
 
@@ -255,6 +268,7 @@ int enqueue_finalize(mase_handle *h, int *launches) {
     k_finalize<<<1, 1024, 0, h->stream>>>(X, h->iters.p, h->status.p, h->laststep.p, h->stop.p,
                                          h->n_active.p);
     ++*launches;
+    mark(h, 4);
     CK(cudaMemcpyAsync(h->h_n_active, h->n_active.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return MASE_OK;
 }
@@ -515,6 +529,8 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     ++launches;
     CK(cudaGetLastError());
+    int steps = 0;
+    double stage_ms[4] = {0, 0, 0, 0};
     StopRule rule{tol, max_iter};
     CK(cudaMemcpyAsync(h->stop.p, &rule, sizeof(rule), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -544,6 +560,14 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         }
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
+        ++steps;
+        if (h->opt.profile) {
+            for (int i = 0; i < 4; ++i) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, h->ev_stage[i], h->ev_stage[i + 1]));
+                stage_ms[i] += ms;
+            }
+        }
         if (*h->h_n_active == 0) break;
     }
     int rc = enqueue_objective<RG, RS>(h, &launches);
@@ -580,6 +604,8 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
             if (stats->max_step) stats->max_step[s] = last[s];
         }
         stats->total_launches = launches;
+        stats->steps = steps;
+        for (int i = 0; i < 4; ++i) stats->stage_ms[i] = stage_ms[i];
     }
     if (ret == MASE_EUNOBSERVABLE) set_err(ret, "non-positive pivot in an area or boundary factor");
     if (ret == MASE_ENONFINITE) set_err(ret, "non-finite step");
@@ -600,6 +626,7 @@ void mase_default_options(mase_options *o) {
     o->threads = 0;
     o->device = 0;
     o->stream = nullptr;
+    o->profile = 0;
 }
 
 const char *mase_status_str(int code) {
@@ -646,6 +673,7 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    for (auto &e : h->ev_stage) CK(cudaEventCreate(&e));
     {
         int rc0 = join_in(h.get());
         if (rc0 != MASE_OK) return rc0;

@@ -44,12 +44,13 @@ class Measurements(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("profile", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", _i32p), ("status", _i32p), ("J", _f64p), ("max_step", _f64p),
-                ("stage_ms", C.c_double * 4), ("total_launches", C.c_int32)]
+                ("stage_ms", C.c_double * 4), ("total_launches", C.c_int32),
+                ("steps", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -186,13 +187,16 @@ class SolveResult:
     J: np.ndarray
     max_step: np.ndarray
     launches: int
+    steps: int
+    stage_ms: tuple
 
 
 class Estimator:
     """One handle: a network, its partition and a batch of n_snap snapshots."""
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
-                 schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None):
+                 schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
+                 profile=False):
         self.lib = load()
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -200,6 +204,7 @@ class Estimator:
         opt.precision, opt.schedule, opt.use_graph = precision, schedule, int(bool(use_graph))
         opt.refine, opt.threads, opt.device = refine, threads, device
         opt.stream = C.c_void_p(stream) if stream else None
+        opt.profile = int(bool(profile))
         meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
         h = C.c_void_p()
         rc = self.lib.mase_create(C.byref(net), C.byref(part), C.byref(meas), C.byref(opt), C.byref(h))
@@ -245,7 +250,8 @@ class Estimator:
         rc = self.lib.mase_solve(self.h, _ptr(x0), float(tol), int(max_iter), _ptr(x_out), C.byref(st))
         if check and rc < 0:
             raise MaseError(rc, _last_error())
-        return SolveResult(rc, iters, status, J, ms, int(st.total_launches))
+        return SolveResult(rc, iters, status, J, ms, int(st.total_launches), int(st.steps),
+                           tuple(st.stage_ms))
 
     def measure(self, x, z_out, n_snap=None):
         n = self.n_snap if n_snap is None else n_snap

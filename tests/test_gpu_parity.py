@@ -199,7 +199,9 @@ def test_repeat_solves_and_launch_counts(mase):
     r2 = est.solve(tol=1e-8, max_iter=20, x_out=x2)
     est.close()
     assert np.array_equal(r1.iters, r2.iters)
-    assert np.max(np.abs(x1 - x2)) < 1e-10
+    # FP32 atomic accumulation order varies between runs; the converged states
+    # agree to within the stopping tolerance
+    assert np.max(np.abs(x1 - x2)) < 1e-8
     it = int(r1.iters.max())
     # reset + state-in + 4 per step (local, boundary, back, bookkeeping) + objective + state-out
     assert r1.launches == 2 + 4 * it + 2
