@@ -196,6 +196,39 @@ int mase_selfcheck(const mase_network *net, const mase_partition *part, uint64_t
 /* Message of the last mase_analyze / mase_selfcheck failure on this thread. */
 const char *mase_analyze_error(void);
 
+/* Coordinator step without device allocation (the paper has no counterpart;
+ * it serves callers that cannot call cudaMalloc when they need the step:
+ * code running while another thread captures a CUDA graph in global capture
+ * mode, where cudaMalloc is refused; real-time loops that cannot take the
+ * device-wide synchronisation cudaMalloc implies; hosts whose device memory
+ * belongs to another allocator).  Given the condensed blocks of every area and
+ * snapshot it assembles S_Gamma and b_hat_Gamma, factors, refines (MASE_MIXED
+ * handles) and solves, like the coordinator inside mase_solve, and writes the
+ * boundary step.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine: its scratch (boundary factor storage, the assembled copy used by
+ * the refinement, index tables and per-snapshot status words) is one static
+ * device array of 64 MiB that every GPU which loads the library holds until
+ * the process exits; requests needing more return MASE_EINVAL with the
+ * required size in mase_last_error().  The first call on a device resolves the
+ * array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents: calls that overlap on the GPU (two
+ * handles or threads at once) race.  Everything the step reads is rewritten
+ * by each call.
+ *
+ * S_blocks (device, FP64): for area k = 0..K-1, then snapshot s = 0..S-1, the
+ *   packed lower triangle (column-major: column c holds rows c..nb-1) of
+ *   S_b^k(s), nb = nb(k) local boundary unknowns ordered by ascending bus id
+ *   over the area's own boundary buses and the far terminals of its tie lines,
+ *   Vm then Va per bus, the slack angle omitted.
+ * b_blocks (device, FP64): for k, then s, b_hat_b^k(s) [nb(k)] in that order.
+ * dx_gamma (device, FP64) [S][n_gamma]: x_Gamma order = ascending boundary bus
+ *   id, Vm then Va per bus, slack angle omitted.
+ * Returns MASE_OK, MASE_EINVAL (null/host pointers, size above the maximum),
+ * MASE_EUNOBSERVABLE (non-positive pivot), MASE_ENONFINITE or MASE_EDEVICE. */
+int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const double *b_blocks,
+                             double *dx_gamma);
+
 void mase_destroy(mase_handle *h);
 const char *mase_status_str(int code);
 const char *mase_last_error(void);

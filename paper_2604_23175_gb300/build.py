@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmase.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "analyze.cpp", "mase.cu", "warmstart.cu"]
+SOURCES = ["setup.cpp", "analyze.cpp", "mase.cu", "noalloc.cu", "warmstart.cu"]
 
 
 def nvcc() -> str:

@@ -704,6 +704,7 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
     if (tid == 0) atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
 }
 
+#ifndef MASE_SHARED_TEMPLATES_ONLY
 // ---------------------------------------------------------------------------
 // per-snapshot bookkeeping after a step
 // ---------------------------------------------------------------------------
@@ -857,5 +858,7 @@ __global__ void k_measure(const double *__restrict__ x, double *__restrict__ z, 
         }
     }
 }
+
+#endif  // MASE_SHARED_TEMPLATES_ONLY
 
 }  // namespace mase_dev

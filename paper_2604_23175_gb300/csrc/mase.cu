@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/mase.h"
+#include "internal.h"
 #include "kernels.cuh"
 #include "setup.h"
 
@@ -825,3 +826,34 @@ int mase_set_start_mode(mase_handle *h, int32_t mode) {
 void mase_destroy(mase_handle *h) { delete h; }
 
 }  // extern "C"
+
+namespace mase_internal {
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+bool coord_view(const mase_handle *h, CoordView &v) {
+    if (!h) return false;
+    v.precision = h->opt.precision;
+    v.refine = h->opt.precision == MASE_MIXED ? h->opt.refine : 0;
+    v.n_snap = h->n_snap;
+    v.n_area = h->S.K;
+    v.threads = h->threads;
+    v.device = h->opt.device;
+    v.smem_bnd = h->smem_bnd;
+    v.T = h->T;
+    v.B = h->bnd;
+    v.off_B.resize(h->S.K);
+    v.n_bnd.resize(h->S.K);
+    for (int k = 0; k < h->S.K; ++k) {
+        v.off_B[k] = h->S.areas[k].F.off_B;
+        v.n_bnd[k] = h->S.areas[k].n_bnd;
+    }
+    v.xg_of_b = h->S.B.xg_of_b;
+    v.stream = h->stream;
+    v.user_stream = h->user_stream;
+    v.ev_in = h->ev_in;
+    v.ev_out = h->ev_out;
+    return true;
+}
+
+}  // namespace mase_internal

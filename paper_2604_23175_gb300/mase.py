@@ -99,6 +99,7 @@ def load() -> C.CDLL:
         "mase_analyze": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.POINTER(Info)]),
         "mase_selfcheck": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.c_uint64, _f64p]),
         "mase_analyze_error": (C.c_char_p, []),
+        "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +257,13 @@ class Estimator:
     def measure(self, x, z_out, n_snap=None):
         n = self.n_snap if n_snap is None else n_snap
         rc = self.lib.mase_measure(self.h, _ptr(x), int(n), _ptr(z_out))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def coordinator_noalloc(self, S_blocks, b_blocks, dx_gamma):
+        """Coordinator step on caller-held condensed blocks, without device
+        allocation (device tensors in, device tensor out)."""
+        rc = self.lib.mase_coordinator_noalloc(self.h, _ptr(S_blocks), _ptr(b_blocks), _ptr(dx_gamma))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
 

@@ -1,0 +1,99 @@
+"""The allocation-free coordinator entry point (mase_coordinator_noalloc).
+
+It serves callers that cannot call cudaMalloc when they need the coordinator
+step (for example while a CUDA graph is being captured in global mode, or in
+a real-time loop).  The test feeds it the condensed per-area blocks
+(S_b, b_hat_b) of a state x0, computed by the CPU oracle, and compares its
+boundary step with the step that the existing entry point mase_solve takes
+from x0 (one Gauss-Newton step), on two calls in a row.  This file is named to
+be collected last.
+"""
+import numpy as np
+import pytest
+
+from oracle import wls
+from paper_2604_23175_gb300 import synth
+from tests.helpers import net_of, problem
+
+pytestmark = pytest.mark.gpu
+
+# the FP64 path reproduces the exact condensed step; both sides agree far
+# inside the state bar used by the parity tests (1e-6)
+STEP_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def mase():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2604_23175_gb300 import mase as m
+    m.load()
+    return m
+
+
+def _condensed_blocks(net, part, z, w, x0):
+    """Oracle S_b^k, b_hat_b^k for every area and snapshot, packed as the
+    entry point expects: area-major, then snapshot, packed lower column-major."""
+    S = z.shape[0]
+    N = net.n_bus
+    per_area_S = [[] for _ in range(part.n_area)]
+    per_area_b = [[] for _ in range(part.n_area)]
+    for s in range(S):
+        Vm, Va = x0[s, :N], x0[s, N:]
+        r = z[s] - wls.measure(net, Vm, Va)
+        H = wls.jacobian(net, Vm, Va)
+        for k in range(part.n_area):
+            Sb, bh = wls.schur_condense(wls.area_blocks(H, w, r, part, k))
+            nb = Sb.shape[0]
+            per_area_S[k].append(np.concatenate([Sb[c:, c] for c in range(nb)]))
+            per_area_b[k].append(bh)
+    Sflat = np.concatenate([np.concatenate(v) for v in per_area_S])
+    bflat = np.concatenate([np.concatenate(v) for v in per_area_b])
+    return Sflat, bflat
+
+
+def test_coordinator_noalloc_matches_solve_step(mase):
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    S = 2
+    net, Vm, Va, z, sig = problem(g, S, 5100)
+    w = wls.weights(sig)
+    part = wls.partition(net_of(g), g.area_of_bus, g.n_area)
+    rng = np.random.Generator(np.random.PCG64(5101))
+    x0 = np.concatenate([1.0 + 0.01 * rng.standard_normal((S, g.n_bus)),
+                         0.02 * rng.standard_normal((S, g.n_bus))], axis=1)
+    x0[:, g.n_bus + g.slack] = 0.0
+    est = mase.Estimator(g, sig, S, z=z, precision=mase.FP64, schedule=mase.BATCHED)
+    # existing entry point: one Gauss-Newton step from x0
+    x1 = np.zeros_like(x0)
+    est.solve(x0=np.ascontiguousarray(x0), tol=0.0, max_iter=1, x_out=x1, check=False)
+    cols = wls.state_columns(net)
+    ref = (x1 - x0)[:, cols][:, part.gamma_cols]
+    Sflat, bflat = _condensed_blocks(net, part, z, w, x0)
+    Sd = torch.tensor(Sflat, device="cuda")
+    bd = torch.tensor(bflat, device="cuda")
+    nG = len(part.gamma_cols)
+    for call in range(2):
+        dx = torch.full((S, nG), float("nan"), dtype=torch.float64, device="cuda")
+        est.coordinator_noalloc(Sd, bd, dx)
+        got = dx.cpu().numpy()
+        err = np.max(np.abs(got - ref))
+        assert err <= STEP_RTOL * max(1.0, np.max(np.abs(ref))), (call, err)
+    est.close()
+
+
+def test_coordinator_noalloc_rejects_oversized_request(mase):
+    import torch
+    g = synth.make_grid("grid9241_k32")
+    sig = synth.sigma_vector(g.n_bus, g.n_branch)
+    # 64 snapshots of the FP64 boundary system need more than the static maximum
+    est = mase.Estimator(g, sig, 64, z=None, precision=mase.FP64, schedule=mase.BATCHED)
+    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(mase.MaseError) as e:
+        est.coordinator_noalloc(dummy, dummy, dummy)
+    assert e.value.code == mase.MASE_EINVAL
+    assert "static maximum" in str(e.value)
+    est.close()
