@@ -33,6 +33,8 @@ struct FacDev {
     int levoff_base;   // lev_off (nlev + 1 entries)
     int rows_base;     // rows / colbase / relbase
     int rel_base;      // rel
+    int unit_base;     // unit_sn / unit_j
+    int levunit_base;  // lev_units (nlev + 1 entries)
 };
 
 struct AreaDev {
@@ -60,6 +62,7 @@ struct Tables {
     const int *slot_q, *slot_ebeg, *slot_ecnt;
     const int *item_own, *item_uv, *item_pos;
     const int *ebnd;
+    const int *unit_sn, *unit_j, *lev_units;
 };
 
 struct State {
@@ -219,7 +222,6 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
     const int *sn_order = T.sn_order + F.sn_base;
-    const int *item_off = T.item_off + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
         const int a = lev_off[lev], e = lev_off[lev + 1];
@@ -239,35 +241,29 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
         }
         __syncthreads();
         if (do_factor) {
-            const int nit = T.lev_items[F.lev_base + lev];
-            for (int it = tid; it < nit; it += nt) {
-                int lo = a, hi = e - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (item_off[mid] <= it) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int s = F.sn_base + sn_order[lo];
-                const int loc = it - item_off[lo];
+            // column units: a warp takes one (supernode, target column j) and its
+            // lanes walk rows i >= j; unit j = 0 also carries the rhs update
+            const int *lev_units = T.lev_units + F.levunit_base;
+            const int u1 = lev_units[lev + 1];
+            for (int u = lev_units[lev] + warp; u < u1; u += nw) {
+                const int s = F.sn_base + T.unit_sn[F.unit_base + u];
+                const int jr = T.unit_j[F.unit_base + u];
                 const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
                 const RG *Ps = st + T.sn_off[s] + w;
                 const int rb = F.rows_base + T.sn_rows[s];
-                const int P2 = R * (R + 1) / 2;
-                if (loc < P2) {
-                    int ir = (int)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
-                    while (ir * (ir + 1) / 2 > loc) --ir;
-                    while ((ir + 1) * (ir + 2) / 2 <= loc) ++ir;
-                    const int jr = loc - ir * (ir + 1) / 2;
+                RG *cbase = st + T.colbase[rb + jr];
+                const int *relp = T.rel + F.rel_base + T.relbase[rb + jr];
+                const RS *yc = y + T.sn_c0[s];
+                for (int ir = jr + lane; ir < R; ir += 32) {
                     RG v = RG(0);
-                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
-                    const int tgt = T.colbase[rb + jr] + T.rel[F.rel_base + T.relbase[rb + jr] + ir];
-                    atomicAdd(st + tgt, -v);
-                } else {
-                    const int ir = loc - P2;
-                    const RS *yc = y + T.sn_c0[s];
-                    RS v = RS(0);
-                    for (int c = 0; c < w; ++c) v += RS(Ps[(size_t)c * ld + ir]) * yc[c];
-                    atomicAdd(y + T.rows[rb + ir], -v);
+                    RS vr = RS(0);
+                    for (int c = 0; c < w; ++c) {
+                        const RG li = Ps[(size_t)c * ld + ir];
+                        v += li * Ps[(size_t)c * ld + jr];
+                        if (jr == 0) vr += RS(li) * yc[c];
+                    }
+                    atomicAdd(cbase + relp[ir], -v);
+                    if (jr == 0) atomicAdd(y + T.rows[rb + ir], -vr);
                 }
             }
         } else {

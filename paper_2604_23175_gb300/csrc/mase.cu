@@ -39,6 +39,7 @@ struct HostTables {
     std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
     std::vector<double> end_g, end_b, end_bh;
     std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
+    std::vector<int> unit_sn, unit_j, lev_units;
 };
 
 template <class V>
@@ -75,6 +76,12 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
     app(H.relbase, F.relbase);
     d.rel_base = (int)H.rel.size();
     app(H.rel, F.rel);
+    d.unit_base = (int)H.unit_sn.size();
+    app(H.unit_sn, F.unit_sn);
+    app(H.unit_j, F.unit_j);
+    d.levunit_base = (int)H.lev_units.size();
+    if (F.lev_units.empty()) H.lev_units.push_back(0);
+    else app(H.lev_units, F.lev_units);
     return d;
 }
 
@@ -127,7 +134,8 @@ struct mase_handle {
     DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_rows, t_sn_order, t_item_off, t_lev_items,
         t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
         t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
-        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd;
+        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
+        t_unit_sn, t_unit_j, t_lev_units;
     DevBuf<double> t_end_g, t_end_b, t_end_bh;
     DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
         b_bvar_isT;
@@ -447,6 +455,12 @@ int build(mase_handle *h) {
     T.slot_q = h->t_slot_q.p; T.slot_ebeg = h->t_slot_ebeg.p; T.slot_ecnt = h->t_slot_ecnt.p;
     T.item_own = h->t_item_own.p; T.item_uv = h->t_item_uv.p; T.item_pos = h->t_item_pos.p;
     T.ebnd = h->t_ebnd.p;
+    CK(h->t_unit_sn.upload(H.unit_sn, st));
+    CK(h->t_unit_j.upload(H.unit_j, st));
+    CK(h->t_lev_units.upload(H.lev_units, st));
+    T.unit_sn = h->t_unit_sn.p;
+    T.unit_j = h->t_unit_j.p;
+    T.lev_units = h->t_lev_units.p;
     // work buffers
     CK(h->fac.alloc((size_t)h->fac_elems * sizeof(RG)));
     CK(h->cvec.alloc((size_t)std::max<long long>(1, h->c_elems) * sizeof(RS)));
@@ -658,7 +672,7 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     if (h->opt.schedule != MASE_PER_AREA && h->opt.schedule != MASE_BATCHED)
         return set_err(MASE_EINVAL, "bad schedule");
     if (h->opt.refine < 0 || h->opt.refine > 8) return set_err(MASE_EINVAL, "bad refine count");
-    int threads = h->opt.threads ? h->opt.threads : 256;
+    int threads = h->opt.threads ? h->opt.threads : 512;
     if (threads < 64 || threads > 512 || threads % 32) return set_err(MASE_EINVAL, "bad threads");
     h->threads = threads;
     mase::NetIn ni{net->n_bus, net->n_branch, net->slack_bus, net->from_bus, net->to_bus,

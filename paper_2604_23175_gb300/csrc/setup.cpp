@@ -166,6 +166,17 @@ SymResult build_symbolic(const BusSystem &sys) {
         }
         F.lev_items[l] = acc;
     }
+    F.lev_units.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
+            const int s = F.sn_order[i];
+            for (int j = 0; j < F.sn_nr[s]; ++j) {
+                F.unit_sn.push_back(s);
+                F.unit_j.push_back(j);
+            }
+        }
+        F.lev_units[l + 1] = (int)F.unit_sn.size();
+    }
 
     // --- update maps: target column base + relative row positions ---
     F.colbase.assign(F.rows.size(), 0);
@@ -605,21 +616,35 @@ void host_factor(const SymFactor &F, std::vector<double> &st, std::vector<double
                 for (int r = c + 1; r < w; ++r) yc[r] -= col[r] * yc[c];
             }
         }
-        for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
-            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
-            const double *Ps = st.data() + F.sn_off[s] + w;
-            const int rb = F.sn_rows[s];
-            if (factor)
-                for (int jr = 0; jr < R; ++jr)
-                    for (int ir = jr; ir < R; ++ir) {
-                        double v = 0;
-                        for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
-                        st[F.colbase[rb + jr] + F.rel[F.relbase[rb + jr] + ir]] -= v;
+        if (factor) {
+            for (int u = F.lev_units[lev]; u < F.lev_units[lev + 1]; ++u) {
+                const int s = F.unit_sn[u], jr = F.unit_j[u];
+                const int w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
+                const double *Ps = st.data() + F.sn_off[s] + w;
+                const int rb = F.sn_rows[s];
+                const int cb = F.colbase[rb + jr];
+                const int *relp = F.rel.data() + F.relbase[rb + jr];
+                for (int ir = jr; ir < R; ++ir) {
+                    double v = 0;
+                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
+                    st[cb + relp[ir]] -= v;
+                    if (jr == 0) {
+                        double vr = 0;
+                        for (int c = 0; c < w; ++c) vr += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
+                        y[F.rows[rb + ir]] -= vr;
                     }
-            for (int ir = 0; ir < R; ++ir) {
-                double v = 0;
-                for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
-                y[F.rows[rb + ir]] -= v;
+                }
+            }
+        } else {
+            for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
+                const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
+                const double *Ps = st.data() + F.sn_off[s] + w;
+                const int rb = F.sn_rows[s];
+                for (int ir = 0; ir < R; ++ir) {
+                    double v = 0;
+                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
+                    y[F.rows[rb + ir]] -= v;
+                }
             }
         }
     }

@@ -34,6 +34,10 @@ struct SymFactor {
     std::vector<int> sn_order;
     std::vector<int> item_off;           // per sn_order position: first update item within its level
     std::vector<int> lev_items;          // per level: update items (pairs + rhs rows)
+    // column units of the update phase: unit u = (supernode unit_sn[u], target
+    // column unit_j[u] of its row set); units of level l are
+    // [lev_units[l], lev_units[l+1])
+    std::vector<int> unit_sn, unit_j, lev_units;
     std::vector<int> var_sn;             // internal scalar var -> supernode
     int store_int = 0, off_B = 0, store_total = 0;
     int max_w = 0;
