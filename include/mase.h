@@ -140,6 +140,11 @@ typedef struct {
     int64_t g_updates;                      /* gain-matrix scalar updates per snapshot */
     int32_t smem_bytes_max;                 /* largest per-area shared-memory need */
     int32_t areas_in_smem;                  /* areas whose factor fits shared memory */
+    int64_t n_supernodes, n_units;          /* over all areas: supernodes, update column units */
+    int32_t max_levels;                     /* deepest level schedule of an area */
+    int32_t max_area_store;                 /* largest per-area factor storage (entries) */
+    int32_t boundary_store;                 /* boundary-system factor storage (entries) */
+    int32_t boundary_levels;                /* levels of the boundary factor */
 } mase_info;
 
 /* Default options: MIXED, BATCHED, graph on, 1 refinement sweep, device 0. */

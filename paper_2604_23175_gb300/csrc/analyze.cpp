@@ -47,7 +47,13 @@ int mase_analyze(const mase_network *net, const mase_partition *part, mase_info 
         info->factor_nnz += A.F.store_total;
         info->local_flops += A.F.flops;
         info->g_updates += A.g_updates;
+        info->n_supernodes += A.F.nsn();
+        info->n_units += (int64_t)A.F.unit_sn.size();
+        info->max_levels = std::max(info->max_levels, A.F.nlev());
+        info->max_area_store = std::max(info->max_area_store, A.F.store_total);
     }
+    info->boundary_store = S.B.F.store_total;
+    info->boundary_levels = S.B.F.nlev();
     info->boundary_flops = S.B.F.flops;
     return MASE_OK;
 }

@@ -346,8 +346,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     double *g = (double *)(smem + A.off_g);
     RS *y = (RS *)(smem + A.off_y);
     double *bV = (double *)(smem + A.off_bus);
-    double *bT = bV + A.nb_loc;
-    double *bC = bT + A.nb_loc;
+    double *bC = bV + A.nb_loc;
     double *bS = bC + A.nb_loc;
     unsigned char *endbuf = smem + A.off_end;
     double2 *inj = (double2 *)(smem + A.off_inj);
@@ -371,7 +370,6 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         double sn, cs;
         sincos(th, &sn, &cs);
         bV[q] = V;
-        bT[q] = th;
         bC[q] = cs;
         bS[q] = sn;
     }

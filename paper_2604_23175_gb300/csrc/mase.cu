@@ -346,21 +346,16 @@ int build(mase_handle *h) {
         d.zrow_base = S.zrow_base[k];
         // dynamic shared memory layout
         const int nv = A.n_int + A.n_bnd;
-        const size_t endstride = std::max<size_t>(16, 4 * sizeof(RG));
-        size_t o = 0;
-        d.off_g = (int)o;
-        o = align16(o + nv * sizeof(double));
-        d.off_y = (int)o;
-        o = align16(o + nv * sizeof(RS));
-        d.off_bus = (int)o;
-        o = align16(o + 4 * (size_t)A.nb_loc * sizeof(double));
-        d.off_end = (int)o;
-        o = align16(o + (size_t)A.n_ends * endstride);
-        d.off_inj = (int)o;
-        o = align16(o + (size_t)A.n_own * 16);
-        d.off_self = (int)o;
-        o = align16(o + 4 * (size_t)A.n_own * sizeof(RG));
-        d.off_st = (int)o;
+        const mase::SmemLayout lay =
+            mase::area_smem_layout(nv, A.nb_loc, A.n_ends, A.n_own, sizeof(RG), sizeof(RS));
+        d.off_g = (int)lay.off_g;
+        d.off_y = (int)lay.off_y;
+        d.off_bus = (int)lay.off_bus;
+        d.off_end = (int)lay.off_end;
+        d.off_inj = (int)lay.off_inj;
+        d.off_self = (int)lay.off_self;
+        d.off_st = (int)lay.off_st;
+        const size_t o = lay.vector_bytes;
         const size_t with_st = o + (size_t)A.F.store_total * sizeof(RG);
         if (with_st <= (size_t)h->smem_limit) {
             d.in_smem = 1;
@@ -385,6 +380,10 @@ int build(mase_handle *h) {
         factor_nnz += A.F.store_total;
         local_flops += A.F.flops;
         gup += A.g_updates;
+        h->info.n_supernodes += A.F.nsn();
+        h->info.n_units += (int64_t)A.F.unit_sn.size();
+        h->info.max_levels = std::max(h->info.max_levels, A.F.nlev());
+        h->info.max_area_store = std::max(h->info.max_area_store, A.F.store_total);
         max_vars = std::max(max_vars, nv);
         max_nb = std::max(max_nb, A.n_bnd);
     }
@@ -487,6 +486,8 @@ int build(mase_handle *h) {
     I.g_updates = gup;
     I.smem_bytes_max = (int)max_local;
     I.areas_in_smem = in_smem_count;
+    I.boundary_store = B.F.store_total;
+    I.boundary_levels = B.F.nlev();
     return MASE_OK;
 }
 
@@ -677,7 +678,12 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     h->threads = threads;
     mase::NetIn ni{net->n_bus, net->n_branch, net->slack_bus, net->from_bus, net->to_bus,
                    net->r, net->x, net->b_charge};
-    if (!mase::build_setup(ni, part->n_area, part->area_of_bus, h->S))
+    {
+        int optin0 = 0;
+        CK(cudaDeviceGetAttribute(&optin0, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->opt.device));
+        h->smem_limit = optin0 - 1024;
+    }
+    if (!mase::build_setup(ni, part->n_area, part->area_of_bus, h->S, h->smem_limit))
         return set_err(MASE_EINVAL, h->S.error);
     const int M = h->S.m;
     for (int i = 0; i < M; ++i)

@@ -16,6 +16,28 @@ inline int packed_col_start(int cb, int nb) { return cb * nb - cb * (cb - 1) / 2
 
 }  // namespace
 
+SmemLayout area_smem_layout(int nv, int nb_loc, int n_ends, int n_own, size_t rg, size_t rs) {
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    SmemLayout L;
+    const size_t endstride = std::max<size_t>(16, 4 * rg);
+    size_t o = 0;
+    L.off_g = o;
+    o = a16(o + (size_t)nv * sizeof(double));
+    L.off_y = o;
+    o = a16(o + (size_t)nv * rs);
+    L.off_bus = o;
+    o = a16(o + 3 * (size_t)nb_loc * sizeof(double));
+    L.off_end = o;
+    o = a16(o + (size_t)n_ends * endstride);
+    L.off_inj = o;
+    o = a16(o + (size_t)n_own * 16);
+    L.off_self = o;
+    o = a16(o + 4 * (size_t)n_own * rg);
+    L.off_st = o;
+    L.vector_bytes = o;
+    return L;
+}
+
 int SymFactor::pos(int r, int c) const {
     if (r < c) std::swap(r, c);
     if (c >= n_int) {
@@ -38,7 +60,7 @@ int SymFactor::pos(int r, int c) const {
     return sn_off[t] + (c - c0) * ld + rp;
 }
 
-SymResult build_symbolic(const BusSystem &sys) {
+SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wmax) {
     const int ni = sys.nb_int, nbn = sys.nb_bnd, n = ni + nbn;
     SymResult out;
     // --- exact minimum degree on the elimination graph (dense bitmap) ---
@@ -98,15 +120,125 @@ SymResult build_symbolic(const BusSystem &sys) {
             ++nchild[S[p][0]];
         }
     }
-    // --- fundamental supernodes over buses ---
+    // --- relaxed supernodes ---
+    // Fundamental supernodes first; then, bottom-up, a supernode absorbs the
+    // child group that adds the fewest explicit zeros if the zeros stay below
+    // a fraction of the merged panel and the group stays narrow.  An
+    // elimination-tree postorder that visits the absorbed child last keeps
+    // every group contiguous; any topological order of the tree gives the
+    // same factor structure, so the fill does not change.
     std::vector<int> sn_first;
-    for (int p = 0; p < ni; ++p) {
-        bool merge = false;
-        if (p > 0 && parent[p - 1] == p && nchild[p] == 1 &&
-            S[p - 1].size() == S[p].size() + 1 &&
-            std::equal(S[p].begin(), S[p].end(), S[p - 1].begin() + 1))
-            merge = true;
-        if (!merge) sn_first.push_back(p);
+    {
+        std::vector<int> f_first;
+        for (int p = 0; p < ni; ++p) {
+            bool merge = p > 0 && parent[p - 1] == p && nchild[p] == 1 &&
+                         S[p - 1].size() == S[p].size() + 1 &&
+                         std::equal(S[p].begin(), S[p].end(), S[p - 1].begin() + 1);
+            if (!merge) f_first.push_back(p);
+        }
+        f_first.push_back(ni);
+        const int nf = (int)f_first.size() - 1;
+        std::vector<int> f_of(ni);
+        for (int f = 0; f < nf; ++f)
+            for (int p = f_first[f]; p < f_first[f + 1]; ++p) f_of[p] = f;
+        std::vector<int> f_par(nf, -1);
+        std::vector<std::vector<int>> f_kids(nf);
+        for (int f = 0; f < nf; ++f) {
+            int top = f_first[f + 1] - 1;
+            if (parent[top] >= 0) {
+                f_par[f] = f_of[parent[top]];
+                f_kids[f_par[f]].push_back(f);
+            }
+        }
+        // group state per fundamental supernode (as the top of its group)
+        std::vector<long long> gw(nf), gzero(nf, 0);   // width (buses), explicit zeros so far
+        std::vector<int> absorbed(nf, -1);
+        const double alpha = relax_alpha;
+        const int wmax = relax_alpha > 0 ? relax_wmax : 0;   // buses per merged supernode
+        for (int t = 0; t < nf; ++t) {
+            const long long wt = f_first[t + 1] - f_first[t];
+            const long long Rt = (long long)S[f_first[t + 1] - 1].size();
+            gw[t] = wt;
+            int best = -1;
+            long long best_z = 0;
+            for (int c : f_kids[t]) {
+                const long long Rc = (long long)S[f_first[c + 1] - 1].size();
+                const long long W = gw[c] + wt;
+                if (W > wmax) continue;
+                const long long z = gzero[c] + gw[c] * (wt + Rt - Rc);
+                const long long nz = W * (W - 1) / 2 + W * Rt;
+                if (z > alpha * (double)nz) continue;
+                if (best < 0 || gw[c] > gw[best] || (gw[c] == gw[best] && z < best_z)) {
+                    best = c;
+                    best_z = z;
+                }
+            }
+            if (best >= 0) {
+                absorbed[t] = best;
+                gw[t] = gw[best] + wt;
+                gzero[t] = best_z;
+            }
+        }
+        // postorder of the fundamental-supernode forest, absorbed child last
+        std::vector<int> new_of_old(ni, -1), group_start;
+        std::vector<char> is_absorbed(nf, 0);
+        for (int t = 0; t < nf; ++t)
+            if (absorbed[t] >= 0) is_absorbed[absorbed[t]] = 1;
+        int next = 0;
+        std::vector<std::pair<int, int>> stack;   // (supernode, next child index)
+        std::vector<std::vector<int>> kids_ord(nf);
+        for (int t = 0; t < nf; ++t) {
+            for (int c : f_kids[t])
+                if (c != absorbed[t]) kids_ord[t].push_back(c);
+            if (absorbed[t] >= 0) kids_ord[t].push_back(absorbed[t]);
+        }
+        for (int root = 0; root < nf; ++root) {
+            if (f_par[root] != -1) continue;
+            stack.push_back({root, 0});
+            while (!stack.empty()) {
+                auto &top = stack.back();
+                const int t = top.first;
+                if (top.second < (int)kids_ord[t].size()) {
+                    const int c = kids_ord[t][top.second++];
+                    stack.push_back({c, 0});
+                    continue;
+                }
+                if (!is_absorbed[t]) group_start.push_back(next);
+                else if (absorbed[f_par[t]] != t) group_start.push_back(next);
+                for (int p = f_first[t]; p < f_first[t + 1]; ++p) new_of_old[p] = next++;
+                stack.pop_back();
+            }
+        }
+        if (next != ni) fail("symbolic: postorder incomplete");
+        // a group starts at the bottom of its chain: recompute starts from the chains
+        std::vector<char> starts(ni + 1, 0);
+        for (int t = 0; t < nf; ++t) {
+            if (is_absorbed[t]) continue;            // t is the top of a group
+            int b = t;
+            while (absorbed[b] >= 0) b = absorbed[b];
+            starts[new_of_old[f_first[b]]] = 1;
+        }
+        // relabel positions, structures and the tree
+        std::vector<int> order_new(n), old_of_new(ni);
+        for (int p = 0; p < ni; ++p) old_of_new[new_of_old[p]] = p;
+        for (int q = 0; q < ni; ++q) order_new[q] = out.order[old_of_new[q]];
+        for (int q = ni; q < n; ++q) order_new[q] = out.order[q];
+        out.order = order_new;
+        for (int q = 0; q < n; ++q) out.pos_of[out.order[q]] = q;
+        for (int q = 0; q < n; ++q) out.var0[q + 1] = out.var0[q] + sys.nvar[out.order[q]];
+        std::vector<std::vector<int>> S2(ni);
+        for (int p = 0; p < ni; ++p) {
+            for (int q : S[p]) S2[new_of_old[p]].push_back(q < ni ? new_of_old[q] : q);
+            std::sort(S2[new_of_old[p]].begin(), S2[new_of_old[p]].end());
+        }
+        S.swap(S2);
+        for (int p = 0; p < ni; ++p) {
+            if (!S[p].empty() && S[p][0] <= p) fail("symbolic: postorder broke the structure");
+            parent[p] = (!S[p].empty() && S[p][0] < ni) ? S[p][0] : -1;
+        }
+        for (int p = 0; p < ni; ++p)
+            if (starts[p]) sn_first.push_back(p);
+        (void)group_start;
     }
     sn_first.push_back(ni);
     const int nsn = (int)sn_first.size() - 1;
@@ -232,7 +364,8 @@ SymResult build_symbolic(const BusSystem &sys) {
 
 // ---------------------------------------------------------------------------
 
-bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st) {
+bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st,
+                 int smem_limit) {
     try {
         const int N = net.n_bus, L = net.n_branch;
         if (N < 2 || L < 1) fail("need at least 2 buses and 1 branch");
@@ -317,6 +450,17 @@ bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st)
                 v.erase(std::unique(v.begin(), v.end()), v.end());
             }
             sym[k] = build_symbolic(sys);
+            if (smem_limit > 0) {
+                int nv = 0, n_ends = 0;
+                for (int i = 0; i < (int)nd.size(); ++i) nv += sys.nvar[i];
+                for (int b : own[k]) n_ends += (int)inc[b].size();
+                const SmemLayout lay = area_smem_layout(nv, (int)nd.size(), n_ends,
+                                                        (int)own[k].size(), 4, 4);
+                const long long budget =
+                    ((long long)smem_limit - (long long)lay.vector_bytes) / 4;
+                if (sym[k].F.store_total > budget) sym[k] = build_symbolic(sys, 0.10, 8);
+                if (sym[k].F.store_total > budget) sym[k] = build_symbolic(sys, 0.0, 0);
+            }
             for (int i = 0; i < (int)nd.size(); ++i) node_of[nd[i]] = -1;
             // internal numbering: internal buses in elimination order, then own boundary buses
             const int ni = sys.nb_int;

@@ -67,7 +67,24 @@ struct SymResult {
 
 // Exact minimum-degree ordering of the internal nodes on the elimination
 // graph, fundamental supernodes, level schedule and update maps.
-SymResult build_symbolic(const BusSystem &sys);
+// relax_alpha bounds the explicit zeros a merge may add (fraction of the
+// merged panel), relax_wmax the merged width in buses; 0 gives fundamental
+// supernodes only.
+SymResult build_symbolic(const BusSystem &sys, double relax_alpha = 0.30, int relax_wmax = 16);
+
+// Dynamic shared-memory layout of the area kernel for one area (byte
+// offsets, 16-byte aligned): FP64 gradient, rhs in the solve type, bus
+// magnitude/cos/sin (FP64), per-end buffer (flows, then gain partials),
+// per-bus weighted injection residuals, per-bus injection self partials, and
+// the factor storage when it fits.
+struct SmemLayout {
+    size_t off_g, off_y, off_bus, off_end, off_inj, off_self, off_st, vector_bytes;
+};
+SmemLayout area_smem_layout(int nv, int nb_loc, int n_ends, int n_own, size_t rg, size_t rs);
+
+// Shared memory one block may use on the target GPU (227 KB opt-in less 1 KB
+// of static shared memory).
+constexpr int kDefaultSmemLimit = 227 * 1024 - 1024;
 
 // ---------------------------------------------------------------------------
 // Complete problem setup
@@ -126,8 +143,11 @@ struct Setup {
     std::string error;
 };
 
-// Returns false (with s.error set) on invalid input.
-bool build_setup(const NetIn &net, int n_area, const int32_t *area_of_bus, Setup &s);
+// Returns false (with s.error set) on invalid input.  An area whose relaxed
+// FP32 factor storage would not fit in smem_limit bytes next to its vectors is
+// rebuilt with less relaxation (smem_limit 0: no limit).
+bool build_setup(const NetIn &net, int n_area, const int32_t *area_of_bus, Setup &s,
+                 int smem_limit = kDefaultSmemLimit);
 
 // Host-only consistency check of a setup with random SPD data on its patterns:
 // out = {slot-map error, Schur-block error, area solve error, boundary solve error}

@@ -60,7 +60,10 @@ class Info(C.Structure):
                 ("max_area_vars", C.c_int32), ("max_area_nb", C.c_int32),
                 ("factor_nnz", C.c_int64), ("local_flops", C.c_int64),
                 ("boundary_flops", C.c_int64), ("g_updates", C.c_int64),
-                ("smem_bytes_max", C.c_int32), ("areas_in_smem", C.c_int32)]
+                ("smem_bytes_max", C.c_int32), ("areas_in_smem", C.c_int32),
+                ("n_supernodes", C.c_int64), ("n_units", C.c_int64), ("max_levels", C.c_int32),
+                ("max_area_store", C.c_int32), ("boundary_store", C.c_int32),
+                ("boundary_levels", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
