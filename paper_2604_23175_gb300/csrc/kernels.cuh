@@ -22,7 +22,8 @@
 
 namespace mase_dev {
 
-constexpr int WIDE = 24;   // supernodes wider than this are factored by the whole block
+// panels up to this width are factored whole by one warp (must match the host's kNarrowPanel)
+constexpr int kNarrowPanelDev = 4;
 
 // Symbolic factor descriptor (all indices relative to its bases).
 struct FacDev {
@@ -33,8 +34,10 @@ struct FacDev {
     int levoff_base;   // lev_off (nlev + 1 entries)
     int rows_base;     // rows / colbase / relbase
     int rel_base;      // rel
-    int unit_base;     // unit_sn / unit_j
+    int unit_base;     // unit_sn / unit_j / unit_rec (8 ints per unit)
     int levunit_base;  // lev_units (nlev + 1 entries)
+    int trsm_base;     // trsm_rec (4 ints per record)
+    int levtrsm_base;  // lev_trsm (nlev + 1 entries)
 };
 
 struct AreaDev {
@@ -63,6 +66,10 @@ struct Tables {
     const int *item_own, *item_uv, *item_pos;
     const int *ebnd;
     const int *unit_sn, *unit_j, *lev_units;
+    const int4 *unit_rec;   // 2 int4 per unit
+    const int4 *trsm_rec;   // 1 int4 per row solve
+    const int *lev_trsm;
+    const int4 *item_rec;   // 1 int4 per injection item
 };
 
 struct State {
@@ -141,8 +148,12 @@ __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, dou
 
 // Right-looking column Cholesky of one supernode panel by one warp
 // (diagonal block + rows below), fused with the forward solve of its rhs.
+// Rows [0, nrow) of the panel are processed: nrow = ld factors the whole
+// panel, nrow = w only its diagonal block (the rows below are then solved by
+// solve_panel_row).
 template <class RG, class RS>
-__device__ void panel_warp(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
+__device__ void panel_warp(RG *P, int w, int ld, int nrow, RS *yc, bool do_factor, int lane,
+                           int *err) {
     for (int c = 0; c < w; ++c) {
         RG *col = P + (size_t)c * ld;
         if (do_factor) {
@@ -154,13 +165,13 @@ __device__ void panel_warp(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
             const RG sd = sqrt(d);
             const RG inv = RG(1) / sd;
             __syncwarp();
-            for (int r = c + 1 + lane; r < ld; r += 32) col[r] *= inv;
+            for (int r = c + 1 + lane; r < nrow; r += 32) col[r] *= inv;
             if (lane == 0) col[c] = sd;
             __syncwarp();
             for (int c2 = c + 1; c2 < w; ++c2) {
                 const RG l = col[c2];
                 RG *col2 = P + (size_t)c2 * ld;
-                for (int r = c2 + lane; r < ld; r += 32) col2[r] -= col[r] * l;
+                for (int r = c2 + lane; r < nrow; r += 32) col2[r] -= col[r] * l;
             }
             __syncwarp();
         }
@@ -170,46 +181,6 @@ __device__ void panel_warp(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
         for (int r = c + 1 + lane; r < w; r += 32) yc[r] -= RS(col[r]) * yv;
         __syncwarp();
     }
-}
-
-// Same panel, by the whole block (wide supernodes near the elimination-tree root).
-template <class RG, class RS>
-__device__ void panel_block(RG *P, int w, int ld, RS *yc, bool do_factor, int *err) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (do_factor) {
-        for (int c = 0; c < w; ++c) {
-            RG *col = P + (size_t)c * ld;
-            __syncthreads();
-            RG d = col[c];
-            if (!(d > RG(0))) {
-                if (tid == 0) *err = 1;
-                d = RG(1);
-            }
-            const RG sd = sqrt(d);
-            const RG inv = RG(1) / sd;
-            __syncthreads();
-            for (int r = c + 1 + tid; r < ld; r += nt) col[r] *= inv;
-            if (tid == 0) col[c] = sd;
-            __syncthreads();
-            const int ncol = w - c - 1;
-            for (int idx = tid; idx < ncol * ld; idx += nt) {
-                const int c2 = c + 1 + idx / ld, r = idx % ld;
-                if (r >= c2) P[(size_t)c2 * ld + r] -= col[r] * col[c2];
-            }
-        }
-        __syncthreads();
-    }
-    if (tid < 32) {
-        for (int c = 0; c < w; ++c) {
-            const RG *col = P + (size_t)c * ld;
-            const RS yv = yc[c] / RS(col[c]);
-            __syncwarp();
-            if (tid == 0) yc[c] = yv;
-            for (int r = c + 1 + tid; r < w; r += 32) yc[r] -= RS(col[r]) * yv;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
 }
 
 // Factor (optionally) and forward-solve the internal supernodes level by
@@ -223,38 +194,69 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
               nw = nt >> 5;
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
+    const int *lev_units = T.lev_units + F.levunit_base;
+    const int *lev_trsm = T.lev_trsm + F.levtrsm_base;
+    const int4 *urec = T.unit_rec + 2 * (long long)F.unit_base;
+    const int4 *trec = T.trsm_rec + F.trsm_base;
+    const int *rel = T.rel + F.rel_base;
+    const int *rows = T.rows + F.rows_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
         const int a = lev_off[lev], e = lev_off[lev + 1];
+        // (1) one warp per supernode: narrow panels whole, wide ones their diagonal block
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
-            const int w = T.sn_w[s];
-            if (w > WIDE) continue;
-            panel_warp<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
-                               lane, err);
-        }
-        for (int i = a; i < e; ++i) {
-            const int s = F.sn_base + sn_order[i];
-            const int w = T.sn_w[s];
-            if (w <= WIDE) continue;
-            panel_block<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
-                                err);
+            const int w = T.sn_w[s], ld = w + T.sn_nr[s];
+            panel_warp<RG, RS>(st + T.sn_off[s], w, ld, w <= kNarrowPanelDev ? ld : w,
+                               y + T.sn_c0[s], do_factor, lane, err);
         }
         __syncthreads();
+        // (2) rows below the diagonal blocks of wide panels: one thread per row,
+        //     forward substitution against the factored diagonal block
+        if (do_factor) {
+            const int t0 = lev_trsm[lev], t1 = lev_trsm[lev + 1];
+            if (t1 > t0) {
+                for (int t = t0 + tid; t < t1; t += nt) {
+                    const int4 r = trec[t];
+                    RG *P = st + r.x;
+                    const int w = r.y, ld = r.z, row = r.w;
+                    for (int c = 0; c < w; ++c) {
+                        const RG *col = P + (size_t)c * ld;
+                        RG v = col[row];
+                        for (int k = 0; k < c; ++k) v -= P[(size_t)k * ld + row] * P[(size_t)k * ld + c];
+                        P[(size_t)c * ld + row] = v / col[c];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // (3) updates of ancestors and of the trailing Schur block
         if (do_factor) {
             // column units: a warp takes one (supernode, target column j) and its
-            // lanes walk rows i >= j; unit j = 0 also carries the rhs update
-            const int *lev_units = T.lev_units + F.levunit_base;
+            // lanes walk rows i >= j; unit j = 0 also carries the rhs update.
+            // Records are packed and the next one is fetched ahead.
             const int u1 = lev_units[lev + 1];
-            for (int u = lev_units[lev] + warp; u < u1; u += nw) {
-                const int s = F.sn_base + T.unit_sn[F.unit_base + u];
-                const int jr = T.unit_j[F.unit_base + u];
-                const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
-                const RG *Ps = st + T.sn_off[s] + w;
-                const int rb = F.rows_base + T.sn_rows[s];
-                RG *cbase = st + T.colbase[rb + jr];
-                const int *relp = T.rel + F.rel_base + T.relbase[rb + jr];
-                const RS *yc = y + T.sn_c0[s];
+            int u = lev_units[lev] + warp;
+            int4 ra = make_int4(0, 0, 0, 0), rb = make_int4(0, 0, 0, 0);
+            if (u < u1) {
+                ra = urec[2 * u];
+                rb = urec[2 * u + 1];
+            }
+            while (u < u1) {
+                const int un = u + nw;
+                int4 na = ra, nb = rb;
+                if (un < u1) {
+                    na = urec[2 * un];
+                    nb = urec[2 * un + 1];
+                }
+                const RG *Ps = st + ra.x;
+                RG *cbase = st + ra.y;
+                const int *relp = rel + ra.z;
+                const int *rws = rows + ra.w;
+                const int w = rb.x, ld = rb.y, jr = rb.z;
+                const int R = ld - w;
+                const RS *yc = y + rb.w;
                 for (int ir = jr + lane; ir < R; ir += 32) {
+                    const int tg = relp[ir];
                     RG v = RG(0);
                     RS vr = RS(0);
                     for (int c = 0; c < w; ++c) {
@@ -262,9 +264,12 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                         v += li * Ps[(size_t)c * ld + jr];
                         if (jr == 0) vr += RS(li) * yc[c];
                     }
-                    atomicAdd(cbase + relp[ir], -v);
-                    if (jr == 0) atomicAdd(y + T.rows[rb + ir], -vr);
+                    atomicAdd(cbase + tg, -v);
+                    if (jr == 0) atomicAdd(y + rws[ir], -vr);
                 }
+                ra = na;
+                rb = nb;
+                u = un;
             }
         } else {
             for (int i = a + warp; i < e; i += nw) {
@@ -481,21 +486,19 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     // ---- E4: injection-row gain terms, one item per pair of buses in the row
     for (int it = tid; it < A.n_items; it += nt) {
         const int ii = A.item_base + it;
-        const int o = T.item_own[ii];
-        const int uv = T.item_uv[ii];
-        const int u = uv & 0xffff, v = uv >> 16;
-        const int sb = T.own_sbeg[A.own1_base + o];
+        const int4 rec = T.item_rec[ii];
+        const int4 pos = reinterpret_cast<const int4 *>(T.item_pos)[ii];
+        const int o = rec.x, eu = rec.y, ev = rec.z;
+        const int cu = rec.w & 0xffff, cv = rec.w >> 16;
         RG pu[4], pv[4];
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            const int sl = t == 0 ? u : v;
+            const int eb = t == 0 ? eu : ev, ec = t == 0 ? cu : cv;
             RG *dst = t == 0 ? pu : pv;
-            if (sl == 0) {
+            if (eb < 0) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) dst[a] = self[4 * o + a];
             } else {
-                const int ss = A.slot_base + sb + sl - 1;
-                const int eb = T.slot_ebeg[ss], ec = T.slot_ecnt[ss];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) dst[a] = RG(0);
                 for (int e = eb; e < eb + ec; ++e) {
@@ -507,8 +510,9 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         }
         // pu = (dP/dV_u, dP/dth_u, dQ/dV_u, dQ/dth_u)
         const RG wp = RG(wt(rP + o)), wq = RG(wt(rQ + o));
-        const int *p4 = T.item_pos + 4 * (long long)ii;
-        if (u == v) {
+        const int p4[4] = {pos.x, pos.y, pos.z, pos.w};
+        const bool u_eq_v = eu == ev;
+        if (u_eq_v) {
             atomicAdd(st + p4[0], wp * pu[0] * pu[0] + wq * pu[2] * pu[2]);
             if (p4[1] >= 0) atomicAdd(st + p4[1], wp * pu[1] * pu[0] + wq * pu[3] * pu[2]);
             if (p4[2] >= 0) atomicAdd(st + p4[2], wp * pu[1] * pu[1] + wq * pu[3] * pu[3]);

@@ -359,6 +359,26 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
         F.flops += (long long)w * R * (R + 1) / 2;
         F.pairs += (long long)R * (R + 1) / 2;
     }
+    F.unit_rec.reserve(8 * F.unit_sn.size());
+    for (size_t u = 0; u < F.unit_sn.size(); ++u) {
+        const int s = F.unit_sn[u], j = F.unit_j[u], w = F.sn_w[s], R = F.sn_nr[s];
+        const int rb = F.sn_rows[s];
+        const int rec[8] = {F.sn_off[s] + w, F.colbase[rb + j], F.relbase[rb + j], rb, w, w + R, j,
+                            F.sn_c0[s]};
+        F.unit_rec.insert(F.unit_rec.end(), rec, rec + 8);
+    }
+    F.lev_trsm.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s];
+            if (w <= kNarrowPanel) continue;
+            for (int r = 0; r < R; ++r) {
+                const int rec[4] = {F.sn_off[s], w, w + R, w + r};
+                F.trsm_rec.insert(F.trsm_rec.end(), rec, rec + 4);
+            }
+        }
+        F.lev_trsm[l + 1] = (int)F.trsm_rec.size() / 4;
+    }
     return out;
 }
 
@@ -638,6 +658,12 @@ bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st,
                             p4[3] = gp(Ta, Tb);
                         }
                         if (p4[0] < 0) fail("injection slot missing");
+                        auto first_end = [&](int u_) { return u_ == 0 ? -1 : A.slot_ebeg[s0 + u_ - 1]; };
+                        auto n_end = [&](int u_) { return u_ == 0 ? 0 : A.slot_ecnt[s0 + u_ - 1]; };
+                        A.item_rec.push_back(o);
+                        A.item_rec.push_back(first_end(u));
+                        A.item_rec.push_back(first_end(v));
+                        A.item_rec.push_back(n_end(u) | (n_end(v) << 16));
                         A.item_own.push_back(o);
                         A.item_uv.push_back(u | (v << 16));
                         for (int a = 0; a < 4; ++a) {

@@ -38,6 +38,12 @@ struct SymFactor {
     // column unit_j[u] of its row set); units of level l are
     // [lev_units[l], lev_units[l+1])
     std::vector<int> unit_sn, unit_j, lev_units;
+    // packed unit records, 8 ints each: {sn_off + w, colbase, relbase,
+    // sn_rows, w, ld, j, c0}
+    std::vector<int> unit_rec;
+    // row solves of wide panels (w > kNarrowPanel): level l owns records
+    // [lev_trsm[l], lev_trsm[l+1]), 4 ints each: {sn_off, w, ld, row}
+    std::vector<int> trsm_rec, lev_trsm;
     std::vector<int> var_sn;             // internal scalar var -> supernode
     int store_int = 0, off_B = 0, store_total = 0;
     int max_w = 0;
@@ -49,6 +55,11 @@ struct SymFactor {
     // storage offset of lower entry (r, c), r >= c; -1 if outside the pattern
     int pos(int r, int c) const;
 };
+
+// Panels up to this width are factored over all their rows by one warp;
+// wider panels factor the diagonal block in one warp and solve the rows below
+// it in parallel, one thread per row.
+constexpr int kNarrowPanel = 4;
 
 // Bus-level system: nodes [0, nb_int) are eliminated in a fill-reducing
 // order, nodes [nb_int, nb_int + nb_bnd) are kept (in the given order).
@@ -114,6 +125,9 @@ struct AreaSetup {
     std::vector<int> slot_q, slot_ebeg, slot_ecnt;
     // injection-row gain items: own bus, slot u, slot v (0 = the bus itself), 4 positions
     std::vector<int> item_own, item_uv, item_pos;  // item_uv = u | v << 16
+    // packed item records, 4 ints each: {own bus, first end of slot u (-1: the
+    // bus itself), first end of slot v, end count u | end count v << 16}
+    std::vector<int> item_rec;
     std::vector<int> ebnd;               // local boundary unknown -> boundary-system scalar index
     std::vector<int> bnd_xg;             // local boundary unknown -> x_Gamma index (oracle order)
     long long work = 0;                  // cost estimate for scheduling
