@@ -22,8 +22,6 @@
 
 namespace mase_dev {
 
-// panels up to this width are factored whole by one warp (must match the host's kNarrowPanel)
-constexpr int kNarrowPanelDev = 4;
 
 // Symbolic factor descriptor (all indices relative to its bases).
 struct FacDev {
@@ -36,8 +34,6 @@ struct FacDev {
     int rel_base;      // rel
     int unit_base;     // unit_sn / unit_j / unit_rec (8 ints per unit)
     int levunit_base;  // lev_units (nlev + 1 entries)
-    int trsm_base;     // trsm_rec (4 ints per record)
-    int levtrsm_base;  // lev_trsm (nlev + 1 entries)
 };
 
 struct AreaDev {
@@ -67,8 +63,6 @@ struct Tables {
     const int *ebnd;
     const int *unit_sn, *unit_j, *lev_units;
     const int4 *unit_rec;   // 2 int4 per unit
-    const int4 *trsm_rec;   // 1 int4 per row solve
-    const int *lev_trsm;
     const int4 *item_rec;   // 1 int4 per injection item
 };
 
@@ -146,39 +140,101 @@ __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, dou
 // supernodal factorisation with trailing Schur block + forward solve
 // ---------------------------------------------------------------------------
 
-// Right-looking column Cholesky of one supernode panel by one warp
-// (diagonal block + rows below), fused with the forward solve of its rhs.
-// Rows [0, nrow) of the panel are processed: nrow = ld factors the whole
-// panel, nrow = w only its diagonal block (the rows below are then solved by
-// solve_panel_row).
+// One warp factors a supernode panel (diagonal block + rows below) and
+// forward-solves its rhs, keeping the working rows in registers.  Columns are
+// processed in blocks of up to 32: the diagonal block of a column block is
+// factored with lane r holding row r (column values are broadcast by
+// shuffles); the rows below it are then solved against it, 32 rows at a time
+// with lane = row, right-looking so that the multiply-adds are independent;
+// finally the remaining columns of the panel receive the block's update.
 template <class RG, class RS>
-__device__ void panel_warp(RG *P, int w, int ld, int nrow, RS *yc, bool do_factor, int lane,
-                           int *err) {
-    for (int c = 0; c < w; ++c) {
-        RG *col = P + (size_t)c * ld;
+__device__ void panel_reg(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
+    constexpr unsigned FULL = 0xffffffffu;
+    for (int kb = 0; kb < w; kb += 32) {
+        const int wb = min(32, w - kb);
+        RG a[32];   // lane r: row kb + r of the diagonal block, columns kb..kb+wb
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            a[c] = (c < wb && lane < wb && c <= lane) ? P[(size_t)(kb + c) * ld + kb + lane] : RG(0);
         if (do_factor) {
-            RG d = col[c];
-            if (!(d > RG(0))) {
-                if (lane == 0) *err = 1;
-                d = RG(1);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < wb) {
+                    RG d = __shfl_sync(FULL, a[c], c);
+                    if (!(d > RG(0))) {
+                        if (lane == 0) *err = 1;
+                        d = RG(1);
+                    }
+                    const RG sd = sqrt(d);
+                    const RG inv = RG(1) / sd;
+                    if (lane == c) a[c] = sd;
+                    else if (lane > c) a[c] *= inv;
+#pragma unroll
+                    for (int c2 = c + 1; c2 < 32; ++c2) {
+                        const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
+                        if (c2 < wb && lane >= c2) a[c2] -= a[c] * l;
+                    }
+                }
             }
-            const RG sd = sqrt(d);
-            const RG inv = RG(1) / sd;
-            __syncwarp();
-            for (int r = c + 1 + lane; r < nrow; r += 32) col[r] *= inv;
-            if (lane == 0) col[c] = sd;
-            __syncwarp();
-            for (int c2 = c + 1; c2 < w; ++c2) {
-                const RG l = col[c2];
-                RG *col2 = P + (size_t)c2 * ld;
-                for (int r = c2 + lane; r < nrow; r += 32) col2[r] -= col[r] * l;
-            }
-            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < wb && lane < wb && c <= lane) P[(size_t)(kb + c) * ld + kb + lane] = a[c];
         }
-        const RS yv = yc[c] / RS(col[c]);
+        // forward solve of the block's rhs (lane r holds y[kb + r])
+        {
+            RS yl = lane < wb ? yc[kb + lane] : RS(0);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < wb) {
+                    const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
+                    if (lane == c) yl = yv;
+                    else if (lane > c && lane < wb) yl -= RS(a[c]) * yv;
+                }
+            }
+            if (lane < wb) yc[kb + lane] = yl;
+        }
         __syncwarp();
-        if (lane == 0) yc[c] = yv;
-        for (int r = c + 1 + lane; r < w; r += 32) yc[r] -= RS(col[r]) * yv;
+        const int kn = kb + wb;
+        // rows below the diagonal block within this panel: rows kb + wb .. ld
+        // (in solve-only mode the rows of R are handled by the update pass)
+        for (int r0 = do_factor ? kn : ld; r0 < ld; r0 += 32) {
+            const int row = r0 + lane;
+            const bool act = row < ld;
+            RG x[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) x[c] = (act && c < wb) ? P[(size_t)(kb + c) * ld + row] : RG(0);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < wb) {
+                    const RG *Lc = P + (size_t)(kb + c) * ld + kb;   // column c of the factored block
+                    x[c] /= Lc[c];
+#pragma unroll
+                    for (int c2 = c + 1; c2 < 32; ++c2)
+                        if (c2 < wb) x[c2] -= x[c] * Lc[c2];
+                }
+            }
+            if (act) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < wb) P[(size_t)(kb + c) * ld + row] = x[c];
+            }
+        }
+        __syncwarp();
+        // update of the panel's remaining columns kb + wb .. w (rows >= column)
+        for (int c2 = do_factor ? kn : w; c2 < w; ++c2) {
+            for (int r = c2 + lane; r < ld; r += 32) {
+                RG v = RG(0);
+                for (int c = 0; c < wb; ++c)
+                    v += P[(size_t)(kb + c) * ld + r] * P[(size_t)(kb + c) * ld + c2];
+                P[(size_t)c2 * ld + r] -= v;
+            }
+        }
+        // rhs of the remaining diagonal-block rows
+        for (int r = kn + lane; r < w; r += 32) {
+            RS v = RS(0);
+            for (int c = 0; c < wb; ++c) v += RS(P[(size_t)(kb + c) * ld + r]) * yc[kb + c];
+            yc[r] -= v;
+        }
         __syncwarp();
     }
 }
@@ -195,41 +251,20 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
     const int *lev_units = T.lev_units + F.levunit_base;
-    const int *lev_trsm = T.lev_trsm + F.levtrsm_base;
     const int4 *urec = T.unit_rec + 2 * (long long)F.unit_base;
-    const int4 *trec = T.trsm_rec + F.trsm_base;
     const int *rel = T.rel + F.rel_base;
     const int *rows = T.rows + F.rows_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
         const int a = lev_off[lev], e = lev_off[lev + 1];
-        // (1) one warp per supernode: narrow panels whole, wide ones their diagonal block
+        // (1) one warp per supernode panel, working rows in registers
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
-            const int w = T.sn_w[s], ld = w + T.sn_nr[s];
-            panel_warp<RG, RS>(st + T.sn_off[s], w, ld, w <= kNarrowPanelDev ? ld : w,
-                               y + T.sn_c0[s], do_factor, lane, err);
+            const int w = T.sn_w[s];
+            panel_reg<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor, lane,
+                              err);
         }
         __syncthreads();
-        // (2) rows below the diagonal blocks of wide panels: one thread per row,
-        //     forward substitution against the factored diagonal block
-        if (do_factor) {
-            const int t0 = lev_trsm[lev], t1 = lev_trsm[lev + 1];
-            if (t1 > t0) {
-                for (int t = t0 + tid; t < t1; t += nt) {
-                    const int4 r = trec[t];
-                    RG *P = st + r.x;
-                    const int w = r.y, ld = r.z, row = r.w;
-                    for (int c = 0; c < w; ++c) {
-                        const RG *col = P + (size_t)c * ld;
-                        RG v = col[row];
-                        for (int k = 0; k < c; ++k) v -= P[(size_t)k * ld + row] * P[(size_t)k * ld + c];
-                        P[(size_t)c * ld + row] = v / col[c];
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // (3) updates of ancestors and of the trailing Schur block
+        // (2) updates of ancestors and of the trailing Schur block
         if (do_factor) {
             // column units: a warp takes one (supernode, target column j) and its
             // lanes walk rows i >= j; unit j = 0 also carries the rhs update.

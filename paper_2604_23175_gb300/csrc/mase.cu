@@ -39,7 +39,7 @@ struct HostTables {
     std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
     std::vector<double> end_g, end_b, end_bh;
     std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
-    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, trsm_rec, lev_trsm, item_rec;
+    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec;
 };
 
 template <class V>
@@ -83,11 +83,6 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
     if (F.lev_units.empty()) H.lev_units.push_back(0);
     else app(H.lev_units, F.lev_units);
     app(H.unit_rec, F.unit_rec);
-    d.trsm_base = (int)H.trsm_rec.size() / 4;
-    app(H.trsm_rec, F.trsm_rec);
-    d.levtrsm_base = (int)H.lev_trsm.size();
-    if (F.lev_trsm.empty()) H.lev_trsm.push_back(0);
-    else app(H.lev_trsm, F.lev_trsm);
     return d;
 }
 
@@ -140,7 +135,7 @@ struct mase_handle {
         t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
         t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
         t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
-        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_trsm_rec, t_lev_trsm, t_item_rec;
+        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec;
     DevBuf<double> t_end_g, t_end_b, t_end_bh;
     DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
         b_bvar_isT;
@@ -467,12 +462,8 @@ int build(mase_handle *h) {
     T.unit_j = h->t_unit_j.p;
     T.lev_units = h->t_lev_units.p;
     CK(h->t_unit_rec.upload(H.unit_rec, st));
-    CK(h->t_trsm_rec.upload(H.trsm_rec.empty() ? std::vector<int>(4, 0) : H.trsm_rec, st));
-    CK(h->t_lev_trsm.upload(H.lev_trsm, st));
     CK(h->t_item_rec.upload(H.item_rec, st));
     T.unit_rec = reinterpret_cast<const int4 *>(h->t_unit_rec.p);
-    T.trsm_rec = reinterpret_cast<const int4 *>(h->t_trsm_rec.p);
-    T.lev_trsm = h->t_lev_trsm.p;
     T.item_rec = reinterpret_cast<const int4 *>(h->t_item_rec.p);
     // work buffers
     CK(h->fac.alloc((size_t)h->fac_elems * sizeof(RG)));

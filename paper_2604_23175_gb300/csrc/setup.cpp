@@ -367,18 +367,6 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
                             F.sn_c0[s]};
         F.unit_rec.insert(F.unit_rec.end(), rec, rec + 8);
     }
-    F.lev_trsm.assign(nlev + 1, 0);
-    for (int l = 0; l < nlev; ++l) {
-        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
-            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s];
-            if (w <= kNarrowPanel) continue;
-            for (int r = 0; r < R; ++r) {
-                const int rec[4] = {F.sn_off[s], w, w + R, w + r};
-                F.trsm_rec.insert(F.trsm_rec.end(), rec, rec + 4);
-            }
-        }
-        F.lev_trsm[l + 1] = (int)F.trsm_rec.size() / 4;
-    }
     return out;
 }
 

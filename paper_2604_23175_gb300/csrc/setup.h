@@ -41,9 +41,7 @@ struct SymFactor {
     // packed unit records, 8 ints each: {sn_off + w, colbase, relbase,
     // sn_rows, w, ld, j, c0}
     std::vector<int> unit_rec;
-    // row solves of wide panels (w > kNarrowPanel): level l owns records
-    // [lev_trsm[l], lev_trsm[l+1]), 4 ints each: {sn_off, w, ld, row}
-    std::vector<int> trsm_rec, lev_trsm;
+
     std::vector<int> var_sn;             // internal scalar var -> supernode
     int store_int = 0, off_B = 0, store_total = 0;
     int max_w = 0;
@@ -55,11 +53,6 @@ struct SymFactor {
     // storage offset of lower entry (r, c), r >= c; -1 if outside the pattern
     int pos(int r, int c) const;
 };
-
-// Panels up to this width are factored over all their rows by one warp;
-// wider panels factor the diagonal block in one warp and solve the rows below
-// it in parallel, one thread per row.
-constexpr int kNarrowPanel = 4;
 
 // Bus-level system: nodes [0, nb_int) are eliminated in a fill-reducing
 // order, nodes [nb_int, nb_int + nb_bnd) are kept (in the given order).
