@@ -140,102 +140,109 @@ __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, dou
 // supernodal factorisation with trailing Schur block + forward solve
 // ---------------------------------------------------------------------------
 
-// One warp factors a supernode panel (diagonal block + rows below) and
-// forward-solves its rhs, keeping the working rows in registers.  Columns are
-// processed in blocks of up to 32: the diagonal block of a column block is
-// factored with lane r holding row r (column values are broadcast by
-// shuffles); the rows below it are then solved against it, 32 rows at a time
-// with lane = row, right-looking so that the multiply-adds are independent;
-// finally the remaining columns of the panel receive the block's update.
+// One column block (columns kb .. kb+wb, wb <= WB) of a supernode panel, by
+// one warp: the diagonal block is factored with lane r holding row r (column
+// values broadcast by shuffles) and its rhs forward-solved; the rows below it
+// are solved 32 at a time with lane = row, right-looking, reading L from
+// shared memory so that the multiply-adds are independent; the panel's
+// remaining columns then receive the block's update.  WB bounds the unrolled
+// loops, so narrow panels run short code.
+template <class RG, class RS, int WB>
+__device__ void panel_colblock(RG *P, int kb, int wb, int w, int ld, RS *yc, bool do_factor,
+                               int lane, int *err) {
+    constexpr unsigned FULL = 0xffffffffu;
+    RG a[WB];   // lane r: row kb + r of the diagonal block
+#pragma unroll
+    for (int c = 0; c < WB; ++c)
+        a[c] = (c < wb && lane < wb && c <= lane) ? P[(size_t)(kb + c) * ld + kb + lane] : RG(0);
+    if (do_factor) {
+#pragma unroll
+        for (int c = 0; c < WB; ++c) {
+            if (c < wb) {
+                RG d = __shfl_sync(FULL, a[c], c);
+                if (!(d > RG(0))) {
+                    if (lane == 0) *err = 1;
+                    d = RG(1);
+                }
+                const RG sd = sqrt(d);
+                const RG inv = RG(1) / sd;
+                if (lane == c) a[c] = sd;
+                else if (lane > c) a[c] *= inv;
+#pragma unroll
+                for (int c2 = c + 1; c2 < WB; ++c2) {
+                    if (c2 < wb) {
+                        const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
+                        if (lane >= c2) a[c2] -= a[c] * l;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < WB; ++c)
+            if (c < wb && lane < wb && c <= lane) P[(size_t)(kb + c) * ld + kb + lane] = a[c];
+    }
+    {
+        RS yl = lane < wb ? yc[kb + lane] : RS(0);
+#pragma unroll
+        for (int c = 0; c < WB; ++c) {
+            if (c < wb) {
+                const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
+                if (lane == c) yl = yv;
+                else if (lane > c && lane < wb) yl -= RS(a[c]) * yv;
+            }
+        }
+        if (lane < wb) yc[kb + lane] = yl;
+    }
+    __syncwarp();
+    const int kn = kb + wb;
+    // rows below the block (in solve-only mode the rows of R are left to the update pass)
+    for (int r0 = do_factor ? kn : ld; r0 < ld; r0 += 32) {
+        const int row = r0 + lane;
+        const bool act = row < ld;
+        RG x[WB];
+#pragma unroll
+        for (int c = 0; c < WB; ++c) x[c] = (act && c < wb) ? P[(size_t)(kb + c) * ld + row] : RG(0);
+#pragma unroll
+        for (int c = 0; c < WB; ++c) {
+            if (c < wb) {
+                const RG *Lc = P + (size_t)(kb + c) * ld + kb;
+                x[c] /= Lc[c];
+#pragma unroll
+                for (int c2 = c + 1; c2 < WB; ++c2)
+                    if (c2 < wb) x[c2] -= x[c] * Lc[c2];
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < WB; ++c)
+                if (c < wb) P[(size_t)(kb + c) * ld + row] = x[c];
+        }
+    }
+    __syncwarp();
+    for (int c2 = do_factor ? kn : w; c2 < w; ++c2) {
+        for (int r = c2 + lane; r < ld; r += 32) {
+            RG v = RG(0);
+            for (int c = 0; c < wb; ++c) v += P[(size_t)(kb + c) * ld + r] * P[(size_t)(kb + c) * ld + c2];
+            P[(size_t)c2 * ld + r] -= v;
+        }
+    }
+    for (int r = kn + lane; r < w; r += 32) {
+        RS v = RS(0);
+        for (int c = 0; c < wb; ++c) v += RS(P[(size_t)(kb + c) * ld + r]) * yc[kb + c];
+        yc[r] -= v;
+    }
+    __syncwarp();
+}
+
 template <class RG, class RS>
 __device__ void panel_reg(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
-    constexpr unsigned FULL = 0xffffffffu;
     for (int kb = 0; kb < w; kb += 32) {
         const int wb = min(32, w - kb);
-        RG a[32];   // lane r: row kb + r of the diagonal block, columns kb..kb+wb
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-            a[c] = (c < wb && lane < wb && c <= lane) ? P[(size_t)(kb + c) * ld + kb + lane] : RG(0);
-        if (do_factor) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                if (c < wb) {
-                    RG d = __shfl_sync(FULL, a[c], c);
-                    if (!(d > RG(0))) {
-                        if (lane == 0) *err = 1;
-                        d = RG(1);
-                    }
-                    const RG sd = sqrt(d);
-                    const RG inv = RG(1) / sd;
-                    if (lane == c) a[c] = sd;
-                    else if (lane > c) a[c] *= inv;
-#pragma unroll
-                    for (int c2 = c + 1; c2 < 32; ++c2) {
-                        const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
-                        if (c2 < wb && lane >= c2) a[c2] -= a[c] * l;
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 32; ++c)
-                if (c < wb && lane < wb && c <= lane) P[(size_t)(kb + c) * ld + kb + lane] = a[c];
-        }
-        // forward solve of the block's rhs (lane r holds y[kb + r])
-        {
-            RS yl = lane < wb ? yc[kb + lane] : RS(0);
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                if (c < wb) {
-                    const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
-                    if (lane == c) yl = yv;
-                    else if (lane > c && lane < wb) yl -= RS(a[c]) * yv;
-                }
-            }
-            if (lane < wb) yc[kb + lane] = yl;
-        }
-        __syncwarp();
-        const int kn = kb + wb;
-        // rows below the diagonal block within this panel: rows kb + wb .. ld
-        // (in solve-only mode the rows of R are handled by the update pass)
-        for (int r0 = do_factor ? kn : ld; r0 < ld; r0 += 32) {
-            const int row = r0 + lane;
-            const bool act = row < ld;
-            RG x[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) x[c] = (act && c < wb) ? P[(size_t)(kb + c) * ld + row] : RG(0);
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                if (c < wb) {
-                    const RG *Lc = P + (size_t)(kb + c) * ld + kb;   // column c of the factored block
-                    x[c] /= Lc[c];
-#pragma unroll
-                    for (int c2 = c + 1; c2 < 32; ++c2)
-                        if (c2 < wb) x[c2] -= x[c] * Lc[c2];
-                }
-            }
-            if (act) {
-#pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (c < wb) P[(size_t)(kb + c) * ld + row] = x[c];
-            }
-        }
-        __syncwarp();
-        // update of the panel's remaining columns kb + wb .. w (rows >= column)
-        for (int c2 = do_factor ? kn : w; c2 < w; ++c2) {
-            for (int r = c2 + lane; r < ld; r += 32) {
-                RG v = RG(0);
-                for (int c = 0; c < wb; ++c)
-                    v += P[(size_t)(kb + c) * ld + r] * P[(size_t)(kb + c) * ld + c2];
-                P[(size_t)c2 * ld + r] -= v;
-            }
-        }
-        // rhs of the remaining diagonal-block rows
-        for (int r = kn + lane; r < w; r += 32) {
-            RS v = RS(0);
-            for (int c = 0; c < wb; ++c) v += RS(P[(size_t)(kb + c) * ld + r]) * yc[kb + c];
-            yc[r] -= v;
-        }
-        __syncwarp();
+        if (wb <= 2) panel_colblock<RG, RS, 2>(P, kb, wb, w, ld, yc, do_factor, lane, err);
+        else if (wb <= 4) panel_colblock<RG, RS, 4>(P, kb, wb, w, ld, yc, do_factor, lane, err);
+        else if (wb <= 8) panel_colblock<RG, RS, 8>(P, kb, wb, w, ld, yc, do_factor, lane, err);
+        else if (wb <= 16) panel_colblock<RG, RS, 16>(P, kb, wb, w, ld, yc, do_factor, lane, err);
+        else panel_colblock<RG, RS, 32>(P, kb, wb, w, ld, yc, do_factor, lane, err);
     }
 }
 
