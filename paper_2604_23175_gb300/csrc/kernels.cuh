@@ -34,6 +34,8 @@ struct FacDev {
     int rel_base;      // rel
     int unit_base;     // unit_sn / unit_j / unit_rec (8 ints per unit)
     int levunit_base;  // lev_units (nlev + 1 entries)
+    int chunk_base;    // chunk_rec (4 ints per chunk)
+    int levchunk_base; // lev_chunks (nlev + 1 entries)
 };
 
 struct AreaDev {
@@ -64,6 +66,8 @@ struct Tables {
     const int *unit_sn, *unit_j, *lev_units;
     const int4 *unit_rec;   // 2 int4 per unit
     const int4 *item_rec;   // 1 int4 per injection item
+    const int4 *chunk_rec;  // 1 int4 per 32-row panel chunk
+    const int *lev_chunks;
 };
 
 struct State {
@@ -140,25 +144,20 @@ __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, dou
 // supernodal factorisation with trailing Schur block + forward solve
 // ---------------------------------------------------------------------------
 
-// One column block (columns kb .. kb+wb, wb <= WB) of a supernode panel, by
-// one warp: the diagonal block is factored with lane r holding row r (column
-// values broadcast by shuffles) and its rhs forward-solved; the rows below it
-// are solved 32 at a time with lane = row, right-looking, reading L from
-// shared memory so that the multiply-adds are independent; the panel's
-// remaining columns then receive the block's update.  WB bounds the unrolled
-// loops, so narrow panels run short code.
+// Diagonal block of a supernode panel (w <= WB <= 32 columns), by one warp:
+// lane r holds row r, column values are broadcast by shuffles; then the
+// block's rhs is forward-solved the same way.
 template <class RG, class RS, int WB>
-__device__ void panel_colblock(RG *P, int kb, int wb, int w, int ld, RS *yc, bool do_factor,
-                               int lane, int *err) {
+__device__ void diag_block(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
     constexpr unsigned FULL = 0xffffffffu;
-    RG a[WB];   // lane r: row kb + r of the diagonal block
+    RG a[WB];
 #pragma unroll
     for (int c = 0; c < WB; ++c)
-        a[c] = (c < wb && lane < wb && c <= lane) ? P[(size_t)(kb + c) * ld + kb + lane] : RG(0);
+        a[c] = (c < w && lane < w && c <= lane) ? P[(size_t)c * ld + lane] : RG(0);
     if (do_factor) {
 #pragma unroll
         for (int c = 0; c < WB; ++c) {
-            if (c < wb) {
+            if (c < w) {
                 RG d = __shfl_sync(FULL, a[c], c);
                 if (!(d > RG(0))) {
                     if (lane == 0) *err = 1;
@@ -170,7 +169,7 @@ __device__ void panel_colblock(RG *P, int kb, int wb, int w, int ld, RS *yc, boo
                 else if (lane > c) a[c] *= inv;
 #pragma unroll
                 for (int c2 = c + 1; c2 < WB; ++c2) {
-                    if (c2 < wb) {
+                    if (c2 < w) {
                         const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
                         if (lane >= c2) a[c2] -= a[c] * l;
                     }
@@ -179,71 +178,62 @@ __device__ void panel_colblock(RG *P, int kb, int wb, int w, int ld, RS *yc, boo
         }
 #pragma unroll
         for (int c = 0; c < WB; ++c)
-            if (c < wb && lane < wb && c <= lane) P[(size_t)(kb + c) * ld + kb + lane] = a[c];
+            if (c < w && lane < w && c <= lane) P[(size_t)c * ld + lane] = a[c];
     }
-    {
-        RS yl = lane < wb ? yc[kb + lane] : RS(0);
+    RS yl = lane < w ? yc[lane] : RS(0);
 #pragma unroll
-        for (int c = 0; c < WB; ++c) {
-            if (c < wb) {
-                const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
-                if (lane == c) yl = yv;
-                else if (lane > c && lane < wb) yl -= RS(a[c]) * yv;
-            }
-        }
-        if (lane < wb) yc[kb + lane] = yl;
-    }
-    __syncwarp();
-    const int kn = kb + wb;
-    // rows below the block (in solve-only mode the rows of R are left to the update pass)
-    for (int r0 = do_factor ? kn : ld; r0 < ld; r0 += 32) {
-        const int row = r0 + lane;
-        const bool act = row < ld;
-        RG x[WB];
-#pragma unroll
-        for (int c = 0; c < WB; ++c) x[c] = (act && c < wb) ? P[(size_t)(kb + c) * ld + row] : RG(0);
-#pragma unroll
-        for (int c = 0; c < WB; ++c) {
-            if (c < wb) {
-                const RG *Lc = P + (size_t)(kb + c) * ld + kb;
-                x[c] /= Lc[c];
-#pragma unroll
-                for (int c2 = c + 1; c2 < WB; ++c2)
-                    if (c2 < wb) x[c2] -= x[c] * Lc[c2];
-            }
-        }
-        if (act) {
-#pragma unroll
-            for (int c = 0; c < WB; ++c)
-                if (c < wb) P[(size_t)(kb + c) * ld + row] = x[c];
+    for (int c = 0; c < WB; ++c) {
+        if (c < w) {
+            const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
+            if (lane == c) yl = yv;
+            else if (lane > c && lane < w) yl -= RS(a[c]) * yv;
         }
     }
-    __syncwarp();
-    for (int c2 = do_factor ? kn : w; c2 < w; ++c2) {
-        for (int r = c2 + lane; r < ld; r += 32) {
-            RG v = RG(0);
-            for (int c = 0; c < wb; ++c) v += P[(size_t)(kb + c) * ld + r] * P[(size_t)(kb + c) * ld + c2];
-            P[(size_t)c2 * ld + r] -= v;
+    if (lane < w) yc[lane] = yl;
+}
+
+// Rows r0 .. r0+32 of a panel below its factored diagonal block, by one warp
+// (lane = row): forward substitution against the block, right-looking so the
+// multiply-adds are independent, L read from shared memory.
+template <class RG, int WB>
+__device__ void panel_rows(RG *P, int w, int ld, int r0, int lane) {
+    const int row = r0 + lane;
+    if (row >= ld) return;
+    RG x[WB];
+#pragma unroll
+    for (int c = 0; c < WB; ++c) x[c] = c < w ? P[(size_t)c * ld + row] : RG(0);
+#pragma unroll
+    for (int c = 0; c < WB; ++c) {
+        if (c < w) {
+            const RG *Lc = P + (size_t)c * ld;
+            x[c] /= Lc[c];
+#pragma unroll
+            for (int c2 = c + 1; c2 < WB; ++c2)
+                if (c2 < w) x[c2] -= x[c] * Lc[c2];
         }
     }
-    for (int r = kn + lane; r < w; r += 32) {
-        RS v = RS(0);
-        for (int c = 0; c < wb; ++c) v += RS(P[(size_t)(kb + c) * ld + r]) * yc[kb + c];
-        yc[r] -= v;
-    }
-    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < WB; ++c)
+        if (c < w) P[(size_t)c * ld + row] = x[c];
 }
 
 template <class RG, class RS>
-__device__ void panel_reg(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
-    for (int kb = 0; kb < w; kb += 32) {
-        const int wb = min(32, w - kb);
-        if (wb <= 2) panel_colblock<RG, RS, 2>(P, kb, wb, w, ld, yc, do_factor, lane, err);
-        else if (wb <= 4) panel_colblock<RG, RS, 4>(P, kb, wb, w, ld, yc, do_factor, lane, err);
-        else if (wb <= 8) panel_colblock<RG, RS, 8>(P, kb, wb, w, ld, yc, do_factor, lane, err);
-        else if (wb <= 16) panel_colblock<RG, RS, 16>(P, kb, wb, w, ld, yc, do_factor, lane, err);
-        else panel_colblock<RG, RS, 32>(P, kb, wb, w, ld, yc, do_factor, lane, err);
-    }
+__device__ __forceinline__ void diag_block_any(RG *P, int w, int ld, RS *yc, bool do_factor,
+                                               int lane, int *err) {
+    if (w <= 2) diag_block<RG, RS, 2>(P, w, ld, yc, do_factor, lane, err);
+    else if (w <= 4) diag_block<RG, RS, 4>(P, w, ld, yc, do_factor, lane, err);
+    else if (w <= 8) diag_block<RG, RS, 8>(P, w, ld, yc, do_factor, lane, err);
+    else if (w <= 16) diag_block<RG, RS, 16>(P, w, ld, yc, do_factor, lane, err);
+    else diag_block<RG, RS, 32>(P, w, ld, yc, do_factor, lane, err);
+}
+
+template <class RG>
+__device__ __forceinline__ void panel_rows_any(RG *P, int w, int ld, int r0, int lane) {
+    if (w <= 2) panel_rows<RG, 2>(P, w, ld, r0, lane);
+    else if (w <= 4) panel_rows<RG, 4>(P, w, ld, r0, lane);
+    else if (w <= 8) panel_rows<RG, 8>(P, w, ld, r0, lane);
+    else if (w <= 16) panel_rows<RG, 16>(P, w, ld, r0, lane);
+    else panel_rows<RG, 32>(P, w, ld, r0, lane);
 }
 
 // Factor (optionally) and forward-solve the internal supernodes level by
@@ -263,32 +253,60 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
     const int *rows = T.rows + F.rows_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
         const int a = lev_off[lev], e = lev_off[lev + 1];
-        // (1) one warp per supernode panel, working rows in registers
+        // (1a) diagonal blocks: one warp per supernode (at most 32 columns)
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
             const int w = T.sn_w[s];
-            panel_reg<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor, lane,
-                              err);
+            diag_block_any<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
+                                   lane, err);
         }
         __syncthreads();
+        // (1b) rows below the diagonal blocks, 32-row chunks spread over all warps
+        if (do_factor) {
+            const int *lev_chunks = T.lev_chunks + F.levchunk_base;
+            const int4 *crec = T.chunk_rec + F.chunk_base;
+            const int k1 = lev_chunks[lev + 1];
+            const int k0 = lev_chunks[lev];
+            if (k1 > k0) {
+                for (int k = k0 + warp; k < k1; k += nw) {
+                    const int4 r = crec[k];
+                    panel_rows_any<RG>(st + r.x, r.y, r.z, r.w, lane);
+                }
+                __syncthreads();
+            }
+        }
         // (2) updates of ancestors and of the trailing Schur block
         if (do_factor) {
             // column units: a warp takes one (supernode, target column j) and its
             // lanes walk rows i >= j; unit j = 0 also carries the rhs update.
             // Records are packed and the next one is fetched ahead.
+            // pipeline: records two units ahead, first target row one unit ahead
             const int u1 = lev_units[lev + 1];
             int u = lev_units[lev] + warp;
-            int4 ra = make_int4(0, 0, 0, 0), rb = make_int4(0, 0, 0, 0);
+            const int4 z4 = make_int4(0, 0, 0, 0);
+            int4 ra = z4, rb = z4, na = z4, nb = z4;
+            int tg0 = 0;
             if (u < u1) {
                 ra = urec[2 * u];
                 rb = urec[2 * u + 1];
+                const int ir = rb.z + lane;
+                if (ir < rb.y - rb.x) tg0 = rel[ra.z + ir];
+            }
+            if (u + nw < u1) {
+                na = urec[2 * (u + nw)];
+                nb = urec[2 * (u + nw) + 1];
             }
             while (u < u1) {
-                const int un = u + nw;
-                int4 na = ra, nb = rb;
+                const int un = u + nw, unn = u + 2 * nw;
+                int tgn = 0;
                 if (un < u1) {
-                    na = urec[2 * un];
-                    nb = urec[2 * un + 1];
+                    const int ir = nb.z + lane;
+                    if (ir < nb.y - nb.x) tgn = rel[na.z + ir];
+                }
+                int4 nna = z4, nnb = z4;
+                if (unn < u1) {
+                    nna = urec[2 * unn];
+                    nnb = urec[2 * unn + 1];
                 }
                 const RG *Ps = st + ra.x;
                 RG *cbase = st + ra.y;
@@ -298,7 +316,7 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                 const int R = ld - w;
                 const RS *yc = y + rb.w;
                 for (int ir = jr + lane; ir < R; ir += 32) {
-                    const int tg = relp[ir];
+                    const int tg = ir < jr + 32 ? tg0 : relp[ir];
                     RG v = RG(0);
                     RS vr = RS(0);
                     for (int c = 0; c < w; ++c) {
@@ -311,6 +329,9 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                 }
                 ra = na;
                 rb = nb;
+                tg0 = tgn;
+                na = nna;
+                nb = nnb;
                 u = un;
             }
         } else {

@@ -39,7 +39,7 @@ struct HostTables {
     std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
     std::vector<double> end_g, end_b, end_bh;
     std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
-    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec;
+    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec, chunk_rec, lev_chunks;
 };
 
 template <class V>
@@ -83,6 +83,11 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
     if (F.lev_units.empty()) H.lev_units.push_back(0);
     else app(H.lev_units, F.lev_units);
     app(H.unit_rec, F.unit_rec);
+    d.chunk_base = (int)H.chunk_rec.size() / 4;
+    app(H.chunk_rec, F.chunk_rec);
+    d.levchunk_base = (int)H.lev_chunks.size();
+    if (F.lev_chunks.empty()) H.lev_chunks.push_back(0);
+    else app(H.lev_chunks, F.lev_chunks);
     return d;
 }
 
@@ -135,7 +140,7 @@ struct mase_handle {
         t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
         t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
         t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
-        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec;
+        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec, t_chunk_rec, t_lev_chunks;
     DevBuf<double> t_end_g, t_end_b, t_end_bh;
     DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
         b_bvar_isT;
@@ -465,6 +470,10 @@ int build(mase_handle *h) {
     CK(h->t_item_rec.upload(H.item_rec, st));
     T.unit_rec = reinterpret_cast<const int4 *>(h->t_unit_rec.p);
     T.item_rec = reinterpret_cast<const int4 *>(h->t_item_rec.p);
+    CK(h->t_chunk_rec.upload(H.chunk_rec.empty() ? std::vector<int>(4, 0) : H.chunk_rec, st));
+    CK(h->t_lev_chunks.upload(H.lev_chunks, st));
+    T.chunk_rec = reinterpret_cast<const int4 *>(h->t_chunk_rec.p);
+    T.lev_chunks = h->t_lev_chunks.p;
     // work buffers
     CK(h->fac.alloc((size_t)h->fac_elems * sizeof(RG)));
     CK(h->cvec.alloc((size_t)std::max<long long>(1, h->c_elems) * sizeof(RS)));

@@ -240,6 +240,25 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
             if (starts[p]) sn_first.push_back(p);
         (void)group_start;
     }
+    // Supernodes wider than kMaxPanel scalars are cut into consecutive pieces:
+    // a piece's structure is the later columns of the supernode plus its rows,
+    // so each piece is a valid supernode and the pieces form a chain.
+    {
+        std::vector<int> cut;
+        sn_first.push_back(ni);
+        for (size_t g = 0; g + 1 < sn_first.size(); ++g) {
+            int p = sn_first[g];
+            const int p1 = sn_first[g + 1];
+            while (p < p1) {
+                cut.push_back(p);
+                int wsc = 0, q = p;
+                while (q < p1 && wsc + sys.nvar[out.order[q]] <= kMaxPanel) wsc += sys.nvar[out.order[q++]];
+                if (q == p) ++q;
+                p = q;
+            }
+        }
+        sn_first.swap(cut);
+    }
     sn_first.push_back(ni);
     const int nsn = (int)sn_first.size() - 1;
     std::vector<int> bus_sn(ni, -1);
@@ -358,6 +377,17 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
             for (int c2 = c + 1; c2 < w; ++c2) F.flops += ld - c2;
         F.flops += (long long)w * R * (R + 1) / 2;
         F.pairs += (long long)R * (R + 1) / 2;
+    }
+    F.lev_chunks.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], ld = w + F.sn_nr[s];
+            for (int r0 = w; r0 < ld; r0 += 32) {
+                const int rec[4] = {F.sn_off[s], w, ld, r0};
+                F.chunk_rec.insert(F.chunk_rec.end(), rec, rec + 4);
+            }
+        }
+        F.lev_chunks[l + 1] = (int)F.chunk_rec.size() / 4;
     }
     F.unit_rec.reserve(8 * F.unit_sn.size());
     for (size_t u = 0; u < F.unit_sn.size(); ++u) {

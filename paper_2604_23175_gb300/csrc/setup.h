@@ -41,6 +41,9 @@ struct SymFactor {
     // packed unit records, 8 ints each: {sn_off + w, colbase, relbase,
     // sn_rows, w, ld, j, c0}
     std::vector<int> unit_rec;
+    // row chunks of the panels below their diagonal blocks: level l owns
+    // records [lev_chunks[l], lev_chunks[l+1]), 4 ints each {sn_off, w, ld, r0}
+    std::vector<int> chunk_rec, lev_chunks;
 
     std::vector<int> var_sn;             // internal scalar var -> supernode
     int store_int = 0, off_B = 0, store_total = 0;
@@ -53,6 +56,10 @@ struct SymFactor {
     // storage offset of lower entry (r, c), r >= c; -1 if outside the pattern
     int pos(int r, int c) const;
 };
+
+// Widest supernode panel, in scalar columns: one warp factors a diagonal block
+// of at most this width in registers.
+constexpr int kMaxPanel = 32;
 
 // Bus-level system: nodes [0, nb_int) are eliminated in a fill-reducing
 // order, nodes [nb_int, nb_int + nb_bnd) are kept (in the given order).
