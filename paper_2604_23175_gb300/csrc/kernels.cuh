@@ -32,7 +32,7 @@ struct FacDev {
     int levoff_base;   // lev_off (nlev + 1 entries)
     int rows_base;     // rows / colbase / relbase
     int rel_base;      // rel
-    int unit_base;     // unit_sn / unit_j / unit_rec (8 ints per unit)
+    int unit_base;     // unit_sn / unit_j / unit_rec (12 ints per unit)
     int levunit_base;  // lev_units (nlev + 1 entries)
     int chunk_base;    // chunk_rec (4 ints per chunk)
     int levchunk_base; // lev_chunks (nlev + 1 entries)
@@ -64,7 +64,7 @@ struct Tables {
     const int *item_own, *item_uv, *item_pos;
     const int *ebnd;
     const int *unit_sn, *unit_j, *lev_units;
-    const int4 *unit_rec;   // 2 int4 per unit
+    const int4 *unit_rec;   // 3 int4 per unit
     const int4 *item_rec;   // 1 int4 per injection item
     const int4 *chunk_rec;  // 1 int4 per 32-row panel chunk
     const int *lev_chunks;
@@ -163,9 +163,10 @@ __device__ void diag_block(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
                     if (lane == 0) *err = 1;
                     d = RG(1);
                 }
-                const RG sd = sqrt(d);
-                const RG inv = RG(1) / sd;
-                if (lane == c) a[c] = sd;
+                // the diagonal entry is stored as its reciprocal 1/L_cc so that
+                // every later solve multiplies instead of dividing
+                const RG inv = rsqrt(d);
+                if (lane == c) a[c] = inv;
                 else if (lane > c) a[c] *= inv;
 #pragma unroll
                 for (int c2 = c + 1; c2 < WB; ++c2) {
@@ -184,7 +185,7 @@ __device__ void diag_block(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
 #pragma unroll
     for (int c = 0; c < WB; ++c) {
         if (c < w) {
-            const RS yv = __shfl_sync(FULL, yl, c) / RS(__shfl_sync(FULL, a[c], c));
+            const RS yv = __shfl_sync(FULL, yl, c) * RS(__shfl_sync(FULL, a[c], c));
             if (lane == c) yl = yv;
             else if (lane > c && lane < w) yl -= RS(a[c]) * yv;
         }
@@ -206,7 +207,7 @@ __device__ void panel_rows(RG *P, int w, int ld, int r0, int lane) {
     for (int c = 0; c < WB; ++c) {
         if (c < w) {
             const RG *Lc = P + (size_t)c * ld;
-            x[c] /= Lc[c];
+            x[c] *= Lc[c];
 #pragma unroll
             for (int c2 = c + 1; c2 < WB; ++c2)
                 if (c2 < w) x[c2] -= x[c] * Lc[c2];
@@ -248,7 +249,7 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
     const int *lev_units = T.lev_units + F.levunit_base;
-    const int4 *urec = T.unit_rec + 2 * (long long)F.unit_base;
+    const int4 *urec = T.unit_rec + 3 * (long long)F.unit_base;
     const int *rel = T.rel + F.rel_base;
     const int *rows = T.rows + F.rows_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
@@ -280,58 +281,70 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
             // column units: a warp takes one (supernode, target column j) and its
             // lanes walk rows i >= j; unit j = 0 also carries the rhs update.
             // Records are packed and the next one is fetched ahead.
-            // pipeline: records two units ahead, first target row one unit ahead
+            // pipeline: records two units ahead, first target row one unit ahead.
+            // A unit covers up to four target columns j0 .. j0+nj of one segment:
+            // each row loads its L values and its target row once.
             const int u1 = lev_units[lev + 1];
             int u = lev_units[lev] + warp;
             const int4 z4 = make_int4(0, 0, 0, 0);
-            int4 ra = z4, rb = z4, na = z4, nb = z4;
+            int4 ra = z4, rb = z4, rc = z4, na = z4, nb = z4, nc = z4;
             int tg0 = 0;
             if (u < u1) {
-                ra = urec[2 * u];
-                rb = urec[2 * u + 1];
+                ra = urec[3 * u];
+                rb = urec[3 * u + 1];
+                rc = urec[3 * u + 2];
                 const int ir = rb.z + lane;
-                if (ir < rb.y - rb.x) tg0 = rel[ra.z + ir];
+                if (ir < rb.y - rb.x) tg0 = rel[ra.y + ir];
             }
             if (u + nw < u1) {
-                na = urec[2 * (u + nw)];
-                nb = urec[2 * (u + nw) + 1];
+                na = urec[3 * (u + nw)];
+                nb = urec[3 * (u + nw) + 1];
+                nc = urec[3 * (u + nw) + 2];
             }
             while (u < u1) {
                 const int un = u + nw, unn = u + 2 * nw;
                 int tgn = 0;
                 if (un < u1) {
                     const int ir = nb.z + lane;
-                    if (ir < nb.y - nb.x) tgn = rel[na.z + ir];
+                    if (ir < nb.y - nb.x) tgn = rel[na.y + ir];
                 }
-                int4 nna = z4, nnb = z4;
+                int4 nna = z4, nnb = z4, nnc = z4;
                 if (unn < u1) {
-                    nna = urec[2 * unn];
-                    nnb = urec[2 * unn + 1];
+                    nna = urec[3 * unn];
+                    nnb = urec[3 * unn + 1];
+                    nnc = urec[3 * unn + 2];
                 }
                 const RG *Ps = st + ra.x;
-                RG *cbase = st + ra.y;
-                const int *relp = rel + ra.z;
-                const int *rws = rows + ra.w;
-                const int w = rb.x, ld = rb.y, jr = rb.z;
+                const int *relp = rel + ra.y;
+                const int *rws = rows + ra.z;
+                const RS *yc = y + ra.w;
+                const int w = rb.x, ld = rb.y, j0 = rb.z, nj = rb.w;
                 const int R = ld - w;
-                const RS *yc = y + rb.w;
-                for (int ir = jr + lane; ir < R; ir += 32) {
-                    const int tg = ir < jr + 32 ? tg0 : relp[ir];
-                    RG v = RG(0);
+                const int cb[4] = {rc.x, rc.y, rc.z, rc.w};
+                for (int ir = j0 + lane; ir < R; ir += 32) {
+                    const int tg = ir < j0 + 32 ? tg0 : relp[ir];
+                    RG v[4] = {RG(0), RG(0), RG(0), RG(0)};
                     RS vr = RS(0);
                     for (int c = 0; c < w; ++c) {
                         const RG li = Ps[(size_t)c * ld + ir];
-                        v += li * Ps[(size_t)c * ld + jr];
-                        if (jr == 0) vr += RS(li) * yc[c];
+                        const RG *lj = Ps + (size_t)c * ld + j0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < nj) v[k] += li * lj[k];
+                        if (j0 == 0) vr += RS(li) * yc[c];
                     }
-                    atomicAdd(cbase + tg, -v);
-                    if (jr == 0) atomicAdd(y + rws[ir], -vr);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nj && ir >= j0 + k) atomicAdd(st + cb[k] + tg, -v[k]);
+                    if (j0 == 0) atomicAdd(y + rws[ir], -vr);
                 }
                 ra = na;
                 rb = nb;
+                rc = nc;
                 tg0 = tgn;
                 na = nna;
                 nb = nnb;
+                nc = nnc;
                 u = un;
             }
         } else {
@@ -378,7 +391,7 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const RG *st, RS *y
                 RS acc = RS(0);
                 for (int r = c + 1 + lane; r < w; r += 32) acc += RS(P[(size_t)c * ld + r]) * y[c0 + r];
                 acc = warp_sum(acc);
-                if (lane == 0) y[c0 + c] = (y[c0 + c] - acc) / RS(P[(size_t)c * ld + c]);
+                if (lane == 0) y[c0 + c] = (y[c0 + c] - acc) * RS(P[(size_t)c * ld + c]);
                 __syncwarp();
             }
         }

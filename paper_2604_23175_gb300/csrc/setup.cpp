@@ -317,17 +317,6 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
         }
         F.lev_items[l] = acc;
     }
-    F.lev_units.assign(nlev + 1, 0);
-    for (int l = 0; l < nlev; ++l) {
-        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
-            const int s = F.sn_order[i];
-            for (int j = 0; j < F.sn_nr[s]; ++j) {
-                F.unit_sn.push_back(s);
-                F.unit_j.push_back(j);
-            }
-        }
-        F.lev_units[l + 1] = (int)F.unit_sn.size();
-    }
 
     // --- update maps: target column base + relative row positions ---
     F.colbase.assign(F.rows.size(), 0);
@@ -389,13 +378,29 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
         }
         F.lev_chunks[l + 1] = (int)F.chunk_rec.size() / 4;
     }
-    F.unit_rec.reserve(8 * F.unit_sn.size());
+    // update units: consecutive target columns of one segment, kUnitCols at most
+    F.lev_units.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
+            const int s = F.sn_order[i], R = F.sn_nr[s], rb = F.sn_rows[s];
+            for (int j = 0; j < R;) {
+                int nj = 1;
+                while (nj < kUnitCols && j + nj < R && F.relbase[rb + j + nj] == F.relbase[rb + j]) ++nj;
+                F.unit_sn.push_back(s);
+                F.unit_j.push_back(j);
+                F.unit_nj.push_back(nj);
+                j += nj;
+            }
+        }
+        F.lev_units[l + 1] = (int)F.unit_sn.size();
+    }
+    F.unit_rec.reserve(12 * F.unit_sn.size());
     for (size_t u = 0; u < F.unit_sn.size(); ++u) {
-        const int s = F.unit_sn[u], j = F.unit_j[u], w = F.sn_w[s], R = F.sn_nr[s];
+        const int s = F.unit_sn[u], j = F.unit_j[u], nj = F.unit_nj[u], w = F.sn_w[s], R = F.sn_nr[s];
         const int rb = F.sn_rows[s];
-        const int rec[8] = {F.sn_off[s] + w, F.colbase[rb + j], F.relbase[rb + j], rb, w, w + R, j,
-                            F.sn_c0[s]};
-        F.unit_rec.insert(F.unit_rec.end(), rec, rec + 8);
+        int rec[12] = {F.sn_off[s] + w, F.relbase[rb + j], rb, F.sn_c0[s], w, w + R, j, nj, 0, 0, 0, 0};
+        for (int k = 0; k < nj; ++k) rec[8 + k] = F.colbase[rb + j + k];
+        F.unit_rec.insert(F.unit_rec.end(), rec, rec + 12);
     }
     return out;
 }
@@ -796,29 +801,32 @@ void host_factor(const SymFactor &F, std::vector<double> &st, std::vector<double
                     if (!(d > 0)) throw std::runtime_error("selfcheck: non-positive pivot");
                     d = std::sqrt(d);
                     for (int r = c + 1; r < ld; ++r) col[r] /= d;
-                    col[c] = d;
+                    col[c] = 1.0 / d;   // diagonal kept as its reciprocal, as on the device
                     for (int c2 = c + 1; c2 < w; ++c2)
                         for (int r = c2; r < ld; ++r) P[(size_t)c2 * ld + r] -= col[r] * col[c2];
                 }
-                yc[c] /= col[c];
+                yc[c] *= col[c];
                 for (int r = c + 1; r < w; ++r) yc[r] -= col[r] * yc[c];
             }
         }
         if (factor) {
             for (int u = F.lev_units[lev]; u < F.lev_units[lev + 1]; ++u) {
-                const int s = F.unit_sn[u], jr = F.unit_j[u];
-                const int w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
-                const double *Ps = st.data() + F.sn_off[s] + w;
-                const int rb = F.sn_rows[s];
-                const int cb = F.colbase[rb + jr];
-                const int *relp = F.rel.data() + F.relbase[rb + jr];
-                for (int ir = jr; ir < R; ++ir) {
-                    double v = 0;
-                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
-                    st[cb + relp[ir]] -= v;
-                    if (jr == 0) {
+                const int *rec = F.unit_rec.data() + 12 * (size_t)u;
+                const double *Ps = st.data() + rec[0];
+                const int *relp = F.rel.data() + rec[1];
+                const int rb = rec[2], c0 = rec[3], w = rec[4], ld = rec[5], j0 = rec[6], nj = rec[7];
+                const int R = ld - w;
+                for (int ir = j0; ir < R; ++ir) {
+                    for (int k = 0; k < nj; ++k) {
+                        const int jr = j0 + k;
+                        if (ir < jr) continue;
+                        double v = 0;
+                        for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
+                        st[rec[8 + k] + relp[ir]] -= v;
+                    }
+                    if (j0 == 0) {
                         double vr = 0;
-                        for (int c = 0; c < w; ++c) vr += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
+                        for (int c = 0; c < w; ++c) vr += Ps[(size_t)c * ld + ir] * y[c0 + c];
                         y[F.rows[rb + ir]] -= vr;
                     }
                 }
@@ -847,7 +855,7 @@ void host_back(const SymFactor &F, const std::vector<double> &st, std::vector<do
                 for (int ir = 0; ir < R; ++ir) y[c0 + c] -= P[(size_t)c * ld + w + ir] * y[F.rows[F.sn_rows[s] + ir]];
             for (int c = w - 1; c >= 0; --c) {
                 for (int r = c + 1; r < w; ++r) y[c0 + c] -= P[(size_t)c * ld + r] * y[c0 + r];
-                y[c0 + c] /= P[(size_t)c * ld + c];
+                y[c0 + c] *= P[(size_t)c * ld + c];
             }
         }
 }

@@ -23,7 +23,8 @@ namespace mase {
 // ld_s = w_s + nr_s rows by w_s columns at sn_off[s]; rows 0..w_s-1 are its
 // diagonal block (lower part used), rows w_s.. are its off-diagonal row set
 // R_s (rows[sn_rows[s] ...], sorted scalar indices).  The Schur block is
-// stored packed lower, column-major, at off_B.
+// stored packed lower, column-major, at off_B.  After the numeric
+// factorisation the diagonal entries hold 1/L_cc.
 struct SymFactor {
     int n_int = 0, n_bnd = 0;
     std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_rows;
@@ -34,12 +35,13 @@ struct SymFactor {
     std::vector<int> sn_order;
     std::vector<int> item_off;           // per sn_order position: first update item within its level
     std::vector<int> lev_items;          // per level: update items (pairs + rhs rows)
-    // column units of the update phase: unit u = (supernode unit_sn[u], target
-    // column unit_j[u] of its row set); units of level l are
-    // [lev_units[l], lev_units[l+1])
-    std::vector<int> unit_sn, unit_j, lev_units;
-    // packed unit records, 8 ints each: {sn_off + w, colbase, relbase,
-    // sn_rows, w, ld, j, c0}
+    // column units of the update phase: unit u covers target columns
+    // unit_j[u] .. unit_j[u] + unit_nj[u] (at most kUnitCols) of supernode
+    // unit_sn[u]'s row set, all in one target segment (they share the
+    // relative-index array); units of level l are [lev_units[l], lev_units[l+1])
+    std::vector<int> unit_sn, unit_j, unit_nj, lev_units;
+    // packed unit records, 12 ints each: {sn_off + w, relbase, sn_rows, c0},
+    // {w, ld, j0, nj}, {colbase of the (up to 4) target columns}
     std::vector<int> unit_rec;
     // row chunks of the panels below their diagonal blocks: level l owns
     // records [lev_chunks[l], lev_chunks[l+1]), 4 ints each {sn_off, w, ld, r0}
@@ -60,6 +62,8 @@ struct SymFactor {
 // Widest supernode panel, in scalar columns: one warp factors a diagonal block
 // of at most this width in registers.
 constexpr int kMaxPanel = 32;
+// Target columns handled together by one update unit.
+constexpr int kUnitCols = 4;
 
 // Bus-level system: nodes [0, nb_int) are eliminated in a fill-reducing
 // order, nodes [nb_int, nb_int + nb_bnd) are kept (in the given order).
