@@ -127,6 +127,13 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 struct EndFlow {
     double P, Q, gc_bs, gs_bc;
 };
+// g cos(theta_ij) + b sin(theta_ij) and g sin(theta_ij) - b cos(theta_ij) only
+__device__ __forceinline__ double2 end_trig(double ci, double si, double cj, double sj, double g,
+                                            double b) {
+    const double c = ci * cj + si * sj;
+    const double s = si * cj - ci * sj;
+    return make_double2(g * c + b * s, g * s - b * c);
+}
 __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, double si, double cj,
                                             double sj, double g, double b, double bh) {
     const double c = ci * cj + si * sj;      // cos(theta_i - theta_j)
@@ -168,12 +175,12 @@ __device__ void diag_block(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
                 const RG inv = rsqrt(d);
                 if (lane == c) a[c] = inv;
                 else if (lane > c) a[c] *= inv;
+                // branch-free so the independent shuffles pipeline; columns >= w
+                // only ever touch entries outside the block
 #pragma unroll
                 for (int c2 = c + 1; c2 < WB; ++c2) {
-                    if (c2 < w) {
-                        const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
-                        if (lane >= c2) a[c2] -= a[c] * l;
-                    }
+                    const RG l = __shfl_sync(FULL, a[c], c2);   // L[c2][c]
+                    a[c2] = lane >= c2 ? a[c2] - a[c] * l : a[c2];
                 }
             }
         }
@@ -203,14 +210,17 @@ __device__ void panel_rows(RG *P, int w, int ld, int r0, int lane) {
     RG x[WB];
 #pragma unroll
     for (int c = 0; c < WB; ++c) x[c] = c < w ? P[(size_t)c * ld + row] : RG(0);
+    // branch-free inner loop; loads beyond column w are replaced by zero
 #pragma unroll
     for (int c = 0; c < WB; ++c) {
         if (c < w) {
             const RG *Lc = P + (size_t)c * ld;
             x[c] *= Lc[c];
 #pragma unroll
-            for (int c2 = c + 1; c2 < WB; ++c2)
-                if (c2 < w) x[c2] -= x[c] * Lc[c2];
+            for (int c2 = c + 1; c2 < WB; ++c2) {
+                const RG l = c2 < w ? Lc[c2] : RG(0);
+                x[c2] -= x[c] * l;
+            }
         }
     }
 #pragma unroll
@@ -325,18 +335,26 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                     const int tg = ir < j0 + 32 ? tg0 : relp[ir];
                     RG v[4] = {RG(0), RG(0), RG(0), RG(0)};
                     RS vr = RS(0);
+                    const bool rhs = j0 == 0;
                     for (int c = 0; c < w; ++c) {
                         const RG li = Ps[(size_t)c * ld + ir];
                         const RG *lj = Ps + (size_t)c * ld + j0;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (k < nj) v[k] += li * lj[k];
-                        if (j0 == 0) vr += RS(li) * yc[c];
+                        // branch-free: loads of absent columns are replaced by zero
+                        const RG l0 = lj[0];
+                        const RG l1 = nj > 1 ? lj[1] : RG(0);
+                        const RG l2 = nj > 2 ? lj[2] : RG(0);
+                        const RG l3 = nj > 3 ? lj[3] : RG(0);
+                        v[0] += li * l0;
+                        v[1] += li * l1;
+                        v[2] += li * l2;
+                        v[3] += li * l3;
+                        const RS yv = rhs ? yc[c] : RS(0);
+                        vr += RS(li) * yv;
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         if (k < nj && ir >= j0 + k) atomicAdd(st + cb[k] + tg, -v[k]);
-                    if (j0 == 0) atomicAdd(y + rws[ir], -vr);
+                    if (rhs) atomicAdd(y + rws[ir], -vr);
                 }
                 ra = na;
                 rb = nb;
@@ -505,17 +523,18 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         if (mode != MODE_FULL) continue;
         const double Vi = bV[qi], Vj = bV[qj];
         const double g_ = T.end_g[ee], b_ = T.end_b[ee], bh_ = T.end_bh[ee];
-        const EndFlow f = end_flow(Vi, Vj, bC[qi], bS[qi], bC[qj], bS[qj], g_, b_, bh_);
+        const double2 tr = end_trig(bC[qi], bS[qi], bC[qj], bS[qj], g_, b_);
+        const double gc_bs = tr.x, gs_bc = tr.y;
         const double ViVj = Vi * Vj;
         // partials w.r.t. (Vi, thi, Vj, thj)
         double dP[4], dQ[4];
-        dP[0] = 2.0 * Vi * g_ - Vj * f.gc_bs;
-        dP[1] = ViVj * f.gs_bc;
-        dP[2] = -Vi * f.gc_bs;
+        dP[0] = 2.0 * Vi * g_ - Vj * gc_bs;
+        dP[1] = ViVj * gs_bc;
+        dP[2] = -Vi * gc_bs;
         dP[3] = -dP[1];
-        dQ[0] = -2.0 * Vi * (b_ + bh_) - Vj * f.gs_bc;
-        dQ[1] = -ViVj * f.gc_bs;
-        dQ[2] = -Vi * f.gs_bc;
+        dQ[0] = -2.0 * Vi * (b_ + bh_) - Vj * gs_bc;
+        dQ[1] = -ViVj * gc_bs;
+        dQ[2] = -Vi * gs_bc;
         dQ[3] = -dQ[1];
         const int o = T.end_own[ee];
         const double2 ij = inj[o];
