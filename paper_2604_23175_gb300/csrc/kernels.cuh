@@ -247,6 +247,35 @@ __device__ __forceinline__ void panel_rows_any(RG *P, int w, int ld, int r0, int
     else panel_rows<RG, 32>(P, w, ld, r0, lane);
 }
 
+// Updates of one unit (NJ target columns j0 .. j0+NJ of a supernode's row
+// set) for the rows i >= j0 held by this lane; RHS adds the rhs update of the
+// supernode (carried by the unit with j0 = 0).
+template <class RG, class RS, int NJ, bool RHS>
+__device__ __forceinline__ void unit_rows(RG *st, RS *y, const RG *Ps, const int *relp,
+                                          const int *rws, const RS *yc, int w, int ld, int j0,
+                                          const int4 cb4, int tg0, int lane) {
+    const int R = ld - w;
+    const int cb[4] = {cb4.x, cb4.y, cb4.z, cb4.w};
+    for (int ir = j0 + lane; ir < R; ir += 32) {
+        const int tg = ir < j0 + 32 ? tg0 : relp[ir];
+        RG v[NJ];
+#pragma unroll
+        for (int k = 0; k < NJ; ++k) v[k] = RG(0);
+        RS vr = RS(0);
+        for (int c = 0; c < w; ++c) {
+            const RG li = Ps[(size_t)c * ld + ir];
+            const RG *lj = Ps + (size_t)c * ld + j0;
+#pragma unroll
+            for (int k = 0; k < NJ; ++k) v[k] += li * lj[k];
+            if (RHS) vr += RS(li) * yc[c];
+        }
+#pragma unroll
+        for (int k = 0; k < NJ; ++k)
+            if (ir >= j0 + k) atomicAdd(st + cb[k] + tg, -v[k]);
+        if (RHS) atomicAdd(y + rws[ir], -vr);
+    }
+}
+
 // Factor (optionally) and forward-solve the internal supernodes level by
 // level.  Updates of ancestors -- including the trailing Schur block and the
 // boundary part of the rhs -- are scattered with atomics through the
@@ -329,32 +358,20 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                 const int *rws = rows + ra.z;
                 const RS *yc = y + ra.w;
                 const int w = rb.x, ld = rb.y, j0 = rb.z, nj = rb.w;
-                const int R = ld - w;
-                const int cb[4] = {rc.x, rc.y, rc.z, rc.w};
-                for (int ir = j0 + lane; ir < R; ir += 32) {
-                    const int tg = ir < j0 + 32 ? tg0 : relp[ir];
-                    RG v[4] = {RG(0), RG(0), RG(0), RG(0)};
-                    RS vr = RS(0);
-                    const bool rhs = j0 == 0;
-                    for (int c = 0; c < w; ++c) {
-                        const RG li = Ps[(size_t)c * ld + ir];
-                        const RG *lj = Ps + (size_t)c * ld + j0;
-                        // branch-free: loads of absent columns are replaced by zero
-                        const RG l0 = lj[0];
-                        const RG l1 = nj > 1 ? lj[1] : RG(0);
-                        const RG l2 = nj > 2 ? lj[2] : RG(0);
-                        const RG l3 = nj > 3 ? lj[3] : RG(0);
-                        v[0] += li * l0;
-                        v[1] += li * l1;
-                        v[2] += li * l2;
-                        v[3] += li * l3;
-                        const RS yv = rhs ? yc[c] : RS(0);
-                        vr += RS(li) * yv;
+                if (j0 == 0) {
+                    switch (nj) {
+                        case 1: unit_rows<RG, RS, 1, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 2: unit_rows<RG, RS, 2, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 3: unit_rows<RG, RS, 3, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        default: unit_rows<RG, RS, 4, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
                     }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < nj && ir >= j0 + k) atomicAdd(st + cb[k] + tg, -v[k]);
-                    if (rhs) atomicAdd(y + rws[ir], -vr);
+                } else {
+                    switch (nj) {
+                        case 1: unit_rows<RG, RS, 1, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 2: unit_rows<RG, RS, 2, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 3: unit_rows<RG, RS, 3, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        default: unit_rows<RG, RS, 4, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                    }
                 }
                 ra = na;
                 rb = nb;
