@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4, help="snapshots in the oracle sample")
     ap.add_argument("--comparator-steps", type=int, default=3)
     ap.add_argument("--workload", default=WORKLOAD, help="grid shape (smaller ones for profiling)")
+    ap.add_argument("--train-samples", type=int, default=16384,
+                    help="estimator-solved snapshots for the warm-start networks (0: flat start)")
+    ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--snapshots", type=int, default=N_SNAP)
     return ap.parse_args()
 
@@ -250,6 +253,53 @@ def run_ours(args, dist):
         est.set_measurements(z_dev)
         last["r"] = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
 
+    # ---- learned warm start (untimed set-up): train the per-area networks on
+    # independent snapshots solved by the estimator itself (seeds disjoint from
+    # the benchmark batch)
+    warm = {"trained": False}
+    if args.train_samples >= 256:
+        t0 = time.perf_counter()
+        from paper_2604_23175_gb300 import synth
+        Zs, Xs = [], []
+        nb = args.train_samples // N_SNAP
+        for b in range(nb):
+            Vt, At = synth.make_states(g, N_SNAP, 30000 + 7 * b, walk_len=1)
+            et = synth.make_noise(g, N_SNAP, 30001 + 7 * b)
+            zt = torch.empty((N_SNAP, g.n_meas), dtype=torch.float64, device="cuda")
+            est.measure(torch.tensor(np.concatenate([Vt, At], 1), device="cuda"), zt)
+            zt += torch.tensor(et, device="cuda")
+            est.set_measurements(zt)
+            xt = torch.zeros((N_SNAP, 2 * N), dtype=torch.float64, device="cuda")
+            est.solve(tol=TOL, max_iter=MAX_ITER, x_out=xt)
+            Zs.append(zt)
+            Xs.append(xt)
+        t1 = time.perf_counter()
+        loss = est.warmstart_train(torch.cat(Zs), torch.cat(Xs), epochs=args.train_epochs, batch=256, lr=1e-3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        del Zs, Xs
+        warm = {"trained": True, "samples": nb * N_SNAP, "epochs": args.train_epochs,
+                "final_loss": loss, "data_s": t1 - t0, "train_s": t2 - t1}
+        est.set_measurements(z_dev)
+        # iterations from the flat, previous-snapshot and learned starts
+        rf = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
+        x_flat = x_dev.clone()
+        x0 = x_flat.clone()
+        x0[1:] = x_flat[:-1]
+        x0[0, :N] = 1.0
+        x0[0, N:] = 0.0
+        rp = est.solve(x0=x0, tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
+        est.set_start_mode(mase.START_LEARNED)
+        rl = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
+        warm.update({"iters_flat": float(rf.iters.mean()), "iters_prev": float(rp.iters.mean()),
+                     "iters_learned": float(rl.iters.mean()),
+                     "max_state_diff_learned_vs_flat": float((x_dev - x_flat).abs().max().item())})
+        # value with the flat start, same timing rules, for comparison
+        est.set_start_mode(mase.START_FLAT)
+        tf = time_steps(torch, step, max(3, args.steps // 2), 2, flush)
+        warm["value_flat_start"] = dist.world * N_SNAP / (dist.max(float(np.mean(tf))) * 1e-3)
+        est.set_start_mode(mase.START_LEARNED)
+
     # ---- timed region (device-resident inputs)
     for _ in range(args.warmup):
         step()
@@ -346,7 +396,8 @@ def run_ours(args, dist):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD and N_SNAP == 64 else f"{args.workload} x{N_SNAP} snapshots (profiling case)", "n_bus": g.n_bus, "n_branch": g.n_branch,
                    "n_area": g.n_area, "n_snap": N_SNAP, "precision": "mixed (FP32 gain/factor/Schur, FP64 residual/gradient/refinement/update)",
-                   "schedule": "batched, CUDA graph per iteration", "start": "flat",
+                   "schedule": "batched, CUDA graph per iteration",
+                   "start": "learned (per-area MLP, judged against flat by J)" if warm["trained"] else "flat",
                    "tol": TOL, "max_iter": MAX_ITER, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{dist.world}"},
         "comparator": {"impl": "plain FP64 per-area GPU pipeline (same library, one launch per area and stage)",
@@ -354,6 +405,7 @@ def run_ours(args, dist):
                        "iters_mean": float(np.mean(cres["r"].iters)),
                        "speedup_of_value": (dist.world * N_SNAP / (ms_max * 1e-3)) / (dist.world * N_SNAP / (cmp_ms * 1e-3))},
         "iters": {"mean": float(np.mean(res.iters)), "max": int(res.iters.max())},
+        "warm_start": warm,
         "accuracy": {"max_state_diff_vs_fp64_gpu": float(np.max(np.abs(x_mixed - x_fp64_h))),
                      "all_converged": bool(np.all(res.status == 0))},
         "stages_ms_per_step": {"area": stages[0] / args.steps, "boundary": stages[1] / args.steps,

@@ -234,6 +234,49 @@ const char *mase_analyze_error(void);
 int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const double *b_blocks,
                              double *dx_gamma);
 
+/* ---- learned warm start (not in the paper) ----------------------------------
+ * One MLP per area maps the area's own measurement rows (normalised) to the
+ * (Vm, Va) of its own buses: Linear -> GELU -> Linear -> GELU -> Linear -> GELU
+ * -> Linear, hidden width `hidden`, GELU in its erf form.  Weights and
+ * activations are BF16 with FP32 accumulation on the tensor cores; master
+ * weights and AdamW moments are FP32.  With MASE_START_LEARNED, mase_solve
+ * keeps the proposal per snapshot only where its objective J is below the
+ * flat start's, so Gauss-Newton remains the judge of the proposal. */
+typedef struct {
+    int32_t  hidden;        /* width of the three hidden layers, multiple of 8 (512)   */
+    int32_t  epochs;        /* passes over the training set                            */
+    int32_t  batch;         /* samples per AdamW step, multiple of 8                   */
+    float    lr;            /* peak learning rate (cosine decay to 5 %)                 */
+    float    weight_decay;  /* decoupled weight decay                                   */
+    uint64_t seed;          /* weight initialisation and shuffling                      */
+} mase_warmstart_options;
+
+void mase_warmstart_default_options(mase_warmstart_options *opt);
+
+/* Train the per-area networks on n samples: z[n][m] measurements (canonical
+ * order) and x[n][2N] states the estimator produced for them; both host or
+ * both device pointers.  final_loss (may be NULL) receives the mean
+ * normalised MSE per area over the last epoch.  Replaces any earlier model. */
+int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32_t n,
+                         const mase_warmstart_options *opt, double *final_loss);
+
+/* The networks' proposal x_out[n_snap][2N] for the handle's current
+ * measurements (slack angle 0), without Gauss-Newton.  x_out host or device. */
+int mase_warmstart_predict(mase_handle *h, double *x_out);
+
+/* Save / load the trained networks (weights and normalisation) to a file; a
+ * loaded file must match the handle's network and partition. */
+int mase_warmstart_save(const mase_handle *h, const char *path);
+int mase_warmstart_load(mase_handle *h, const char *path);
+
+/* One forward and backward pass of a single network with the training
+ * kernels, for checking gradients: dims[5] = {d_in, H, H, H, d_out}
+ * (n_layers = 4, H a multiple of 8); params packs W_l[out][in] then b_l for
+ * l = 1..4 (FP32, host); X[batch][d_in], T[batch][d_out] (host).  loss gets
+ * mean((Y - T)^2); grads has the layout of params. */
+int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const float *params,
+                   const float *X, const float *T, float *loss, float *grads);
+
 void mase_destroy(mase_handle *h);
 const char *mase_status_str(int code);
 const char *mase_last_error(void);

@@ -1,5 +1,5 @@
-// Read-only view of a handle's coordinator data for entry points that live
-// in other translation units.
+// Definitions shared by the library's translation units: the handle, device
+// buffers, and views of the handle for entry points in other files.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,9 +7,135 @@
 #include <string>
 #include <vector>
 
+#include "../../include/mase.h"
 #include "kernels.cuh"
 
-struct mase_handle;
+#include "setup.h"
+
+namespace mase_internal {
+
+struct HostTables {
+    std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_rows, sn_order, item_off, lev_items, lev_off;
+    std::vector<int> rows, colbase, relbase, rel;
+    std::vector<int> locbus, qvarV, qvarT, own_q, own_gvv, own_ebeg, own_sbeg;
+    std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
+    std::vector<double> end_g, end_b, end_bh;
+    std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
+    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec, chunk_rec, lev_chunks;
+};
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        release();
+        n = count;
+        if (!count) return cudaSuccess;
+        return cudaMalloc((void **)&p, count * sizeof(T));
+    }
+    cudaError_t upload(const std::vector<T> &v, cudaStream_t st) {
+        cudaError_t e = alloc(v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    }
+};
+
+// true for device or managed memory (asks the CUDA runtime)
+bool is_device_pointer(const void *p);
+
+struct WarmStart;                       // per-area MLP warm start (warmstart.cu)
+void destroy_warmstart(WarmStart *w);
+// Fills (xV, xT) with the learned start for the handle's current measurements
+// and keeps, per snapshot, whichever of the learned and the flat start has
+// the lower objective.  Returns a MASE_* code.
+int learned_start(mase_handle *h, int *launches);
+// Adds r^T W r at the states (xV, xT) to J[s] for every snapshot (area kernel
+// in objective mode); J must be zeroed by the caller.
+void launch_objective(mase_handle *h, double *xV, double *xT, double *J, int *launches);
+
+}  // namespace mase_internal
+
+using mase_internal::DevBuf;
+using mase_internal::HostTables;
+using mase_dev::AreaDev;
+using mase_dev::BndDev;
+using mase_dev::StopRule;
+using mase_dev::Tables;
+
+struct mase_handle {
+    mase::Setup S;
+    mase_options opt{};
+    cudaStream_t stream = nullptr;
+    int n_snap = 0;
+    int start_mode = MASE_START_FLAT;
+    int smem_limit = 0;
+    int threads = 256;
+    // tables
+    HostTables H;
+    std::vector<AreaDev> areas_h;
+    BndDev bnd{};
+    DevBuf<AreaDev> d_areas;
+    DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_rows, t_sn_order, t_item_off, t_lev_items,
+        t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
+        t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
+        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
+        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec, t_chunk_rec, t_lev_chunks;
+    DevBuf<double> t_end_g, t_end_b, t_end_bh;
+    DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
+        b_bvar_isT;
+    Tables T{};
+    DevBuf<int2> d_inst;
+    std::vector<int2> inst_h;
+    // state and measurements
+    DevBuf<double> xV, xT, z_int, z_stage, W;
+    DevBuf<uint8_t> mask_int, mask_stage;
+    bool has_mask = false, has_z = false;
+    DevBuf<int> zperm, bus_of_ibus;
+    // work buffers
+    DevBuf<unsigned char> fac, cvec, bst, bA;
+    DevBuf<double> bh, dxG, J, laststep, xbuf;
+    DevBuf<int> active, err, iters, status, n_active;
+    DevBuf<unsigned long long> maxstep;
+    int *h_n_active = nullptr;   // pinned
+    size_t smem_local = 0, smem_back = 0, smem_bnd = 0;
+    long long fac_elems = 0, c_elems = 0, bh_elems = 0;
+    // measurement function tables (canonical numbering)
+    DevBuf<int> m_from, m_to, m_inc_beg, m_inc_br;
+    DevBuf<double> m_g, m_b, m_bh;
+    // graph
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_launches = 0;
+    DevBuf<StopRule> stop;
+    cudaStream_t user_stream = nullptr;   // caller's stream (NULL = legacy default stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_stage[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    mase_info info{};
+    mase_internal::WarmStart *ws = nullptr;   // learned warm start, if trained or loaded
+    DevBuf<double> xV2, xT2;                  // learned start kept while the flat start is judged
+
+    ~mase_handle() {
+        mase_internal::destroy_warmstart(ws);
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_n_active) cudaFreeHost(h_n_active);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        for (auto &e : ev_stage)
+            if (e) cudaEventDestroy(e);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
 
 namespace mase_internal {
 

@@ -70,6 +70,11 @@ struct Tables {
     const int *lev_chunks;
 };
 
+struct StopRule {
+    double tol;
+    int max_iter;
+};
+
 struct State {
     int N, M, S;                 // buses, measurement rows, snapshots
     double *xV, *xT;             // [S][N] internal bus numbering
@@ -814,15 +819,19 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
     if (tid == 0) atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
 }
 
+// layout conversions (defined below, in the translation unit that includes
+// this header without MASE_SHARED_TEMPLATES_ONLY)
+__global__ void k_gather_rows(const double *__restrict__ src, double *__restrict__ dst,
+                              const int *__restrict__ perm, int M, int S);
+__global__ void k_state_in(const double *__restrict__ x, double *xV, double *xT,
+                           const int *__restrict__ bus_of_ibus, int N, int S, int flat);
+__global__ void k_state_out(double *__restrict__ x, const double *xV, const double *xT,
+                            const int *__restrict__ bus_of_ibus, int N, int S);
+
 #ifndef MASE_SHARED_TEMPLATES_ONLY
 // ---------------------------------------------------------------------------
 // per-snapshot bookkeeping after a step
 // ---------------------------------------------------------------------------
-struct StopRule {
-    double tol;
-    int max_iter;
-};
-
 __global__ void k_finalize(State X, int *iters, int *status, double *laststep,
                            const StopRule *__restrict__ rule, int *n_active) {
     const double tol = rule->tol;

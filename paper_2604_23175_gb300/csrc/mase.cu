@@ -36,15 +36,6 @@ int set_err(int code, const std::string &msg) {
             return set_err(MASE_EDEVICE, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-struct HostTables {
-    std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_rows, sn_order, item_off, lev_items, lev_off;
-    std::vector<int> rows, colbase, relbase, rel;
-    std::vector<int> locbus, qvarV, qvarT, own_q, own_gvv, own_ebeg, own_sbeg;
-    std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
-    std::vector<double> end_g, end_b, end_bh;
-    std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
-    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec, chunk_rec, lev_chunks;
-};
 
 template <class V>
 void app(V &dst, const V &src) {
@@ -96,26 +87,12 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
 }
 
 
-template <class T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t n = 0;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t alloc(size_t count) {
-        n = count;
-        if (!count) return cudaSuccess;
-        return cudaMalloc((void **)&p, count * sizeof(T));
-    }
-    cudaError_t upload(const std::vector<T> &v, cudaStream_t st) {
-        cudaError_t e = alloc(v.size());
-        if (e != cudaSuccess || v.empty()) return e;
-        return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-    }
-};
 
-bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) { return mase_internal::is_device_pointer(p); }
+
+}  // namespace
+
+bool mase_internal::is_device_pointer(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -125,69 +102,10 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+namespace {
+
 }  // namespace
 
-struct mase_handle {
-    mase::Setup S;
-    mase_options opt{};
-    cudaStream_t stream = nullptr;
-    int n_snap = 0;
-    int start_mode = MASE_START_FLAT;
-    int smem_limit = 0;
-    int threads = 256;
-    // tables
-    HostTables H;
-    std::vector<AreaDev> areas_h;
-    BndDev bnd{};
-    DevBuf<AreaDev> d_areas;
-    DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_rows, t_sn_order, t_item_off, t_lev_items,
-        t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
-        t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
-        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
-        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec, t_chunk_rec, t_lev_chunks;
-    DevBuf<double> t_end_g, t_end_b, t_end_bh;
-    DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
-        b_bvar_isT;
-    Tables T{};
-    DevBuf<int2> d_inst;
-    std::vector<int2> inst_h;
-    // state and measurements
-    DevBuf<double> xV, xT, z_int, z_stage, W;
-    DevBuf<uint8_t> mask_int, mask_stage;
-    bool has_mask = false, has_z = false;
-    DevBuf<int> zperm, bus_of_ibus;
-    // work buffers
-    DevBuf<unsigned char> fac, cvec, bst, bA;
-    DevBuf<double> bh, dxG, J, laststep, xbuf;
-    DevBuf<int> active, err, iters, status, n_active;
-    DevBuf<unsigned long long> maxstep;
-    int *h_n_active = nullptr;   // pinned
-    size_t smem_local = 0, smem_back = 0, smem_bnd = 0;
-    long long fac_elems = 0, c_elems = 0, bh_elems = 0;
-    // measurement function tables (canonical numbering)
-    DevBuf<int> m_from, m_to, m_inc_beg, m_inc_br;
-    DevBuf<double> m_g, m_b, m_bh;
-    // graph
-    cudaGraphExec_t graph_exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    int graph_launches = 0;
-    DevBuf<StopRule> stop;
-    cudaStream_t user_stream = nullptr;   // caller's stream (NULL = legacy default stream)
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaEvent_t ev_stage[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    mase_info info{};
-
-    ~mase_handle() {
-        if (graph_exec) cudaGraphExecDestroy(graph_exec);
-        if (graph) cudaGraphDestroy(graph);
-        if (h_n_active) cudaFreeHost(h_n_active);
-        if (ev_in) cudaEventDestroy(ev_in);
-        if (ev_out) cudaEventDestroy(ev_out);
-        for (auto &e : ev_stage)
-            if (e) cudaEventDestroy(e);
-        if (stream) cudaStreamDestroy(stream);
-    }
-};
 
 namespace {
 
@@ -563,6 +481,10 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     ++launches;
     CK(cudaGetLastError());
+    if (!x0 && h->start_mode == MASE_START_LEARNED) {
+        int rc = mase_internal::learned_start(h, &launches);
+        if (rc != MASE_OK) return rc;
+    }
     int steps = 0;
     double stage_ms[4] = {0, 0, 0, 0};
     StopRule rule{tol, max_iter};
@@ -892,6 +814,27 @@ bool coord_view(const mase_handle *h, CoordView &v) {
     v.ev_in = h->ev_in;
     v.ev_out = h->ev_out;
     return true;
+}
+
+}  // namespace mase_internal
+
+namespace mase_internal {
+
+void launch_objective(mase_handle *h, double *xV, double *xT, double *J, int *launches) {
+    State X = make_state(h);
+    X.xV = xV;
+    X.xT = xT;
+    X.J = J;
+    const int grid = h->S.K * h->n_snap;
+    if (h->opt.precision == MASE_MIXED)
+        k_local<float, float><<<grid, h->threads, h->smem_local, h->stream>>>(
+            h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (float *)h->fac.p,
+            (float *)h->cvec.p, h->bh.p);
+    else
+        k_local<double, double><<<grid, h->threads, h->smem_local, h->stream>>>(
+            h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (double *)h->fac.p,
+            (double *)h->cvec.p, h->bh.p);
+    if (launches) ++*launches;
 }
 
 }  // namespace mase_internal

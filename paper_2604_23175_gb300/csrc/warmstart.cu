@@ -1,0 +1,1168 @@
+// Learned warm start: one MLP per area maps the area's own measurement rows
+// to the (Vm, Va) of its own buses (Linear-GELU x3 of width H, then Linear;
+// GELU in its erf form).  Weights and activations are BF16, products are
+// accumulated in FP32 on the tensor cores, and the master weights and AdamW
+// moments are FP32.  The networks are trained on states the estimator itself
+// produced; in mase_solve the proposal is kept per snapshot only where it has
+// a lower WLS objective than the flat start, so Gauss-Newton stays the judge.
+// The paper has no learned component; this file is the warm-start part of
+// the build.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <random>
+#include <string>
+#include <vector>
+
+#define MASE_SHARED_TEMPLATES_ONLY
+#include "internal.h"
+
+using bf16 = __nv_bfloat16;
+
+namespace mase_internal {
+
+namespace {
+
+int fail(int code, const std::string &msg) {
+    set_last_error(msg);
+    return code;
+}
+#define WK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(MASE_EDEVICE, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline int pad8(int x) { return (x + 7) & ~7; }
+
+// ---------------------------------------------------------------------------
+// grouped BF16 GEMM, C(M x N) = A(M x K) * B(K x N), one problem per blockIdx.z
+// ---------------------------------------------------------------------------
+struct GemmProb {
+    const bf16 *A;
+    long long lda;
+    int a_km;            // 1: A(m,k) = A[m*lda + k]; 0: A(m,k) = A[k*lda + m]
+    const bf16 *B;
+    long long ldb;
+    int b_km;            // 1: B(k,n) = B[n*ldb + k]; 0: B(k,n) = B[k*ldb + n]
+    int M, N, K;         // multiples of 8
+    float *Cf;
+    bf16 *Cb;
+    long long ldc;
+    const float *bias;   // [N]
+    bf16 *P_out;         // pre-activation out (hidden layers)
+    const bf16 *P_in;    // pre-activation in (backward through GELU)
+    long long ldp;
+};
+
+enum { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DGELU = 2, EPI_GRAD = 3 };
+
+constexpr int TB = 64, TK = 32, TPAD = 40;
+
+__device__ __forceinline__ float gelu_f(float u) {
+    return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float u) {
+    return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) +
+           u * 0.39894228040143268f * expf(-0.5f * u * u);
+}
+
+// 64 x 32 tile of an operand into shared memory as S[row][k] (k contiguous).
+// All dimensions and offsets are multiples of 8 elements, so every 16-byte
+// chunk is either wholly inside or wholly outside the operand.
+__device__ __forceinline__ void load_tile(bf16 (*S)[TPAD], const bf16 *G, long long ld, int kmajor,
+                                          int r0, int k0, int R, int Kd, int tid) {
+    if (kmajor) {
+        for (int c = tid; c < 256; c += 128) {
+            const int r = c >> 2, kc = (c & 3) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r0 + r < R && k0 + kc < Kd) v = *(const uint4 *)(G + (long long)(r0 + r) * ld + k0 + kc);
+            *(uint4 *)&S[r][kc] = v;
+        }
+    } else {
+        for (int c = tid; c < 256; c += 128) {
+            const int k = c >> 3, rc = (c & 7) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k0 + k < Kd && r0 + rc < R) v = *(const uint4 *)(G + (long long)(k0 + k) * ld + r0 + rc);
+            const bf16 *e = (const bf16 *)&v;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S[rc + i][k] = e[i];
+        }
+    }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_bf16(const GemmProb *__restrict__ probs) {
+    const GemmProb p = probs[blockIdx.z];
+    const int m0 = blockIdx.y * TB, n0 = blockIdx.x * TB;
+    if (m0 >= p.M || n0 >= p.N) return;
+    __shared__ __align__(16) bf16 As[TB][TPAD];
+    __shared__ __align__(16) bf16 Bs[TB][TPAD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    for (int k0 = 0; k0 < p.K; k0 += TK) {
+        load_tile(As, p.A, p.lda, p.a_km, m0, k0, p.M, p.K, tid);
+        load_tile(Bs, p.B, p.ldb, p.b_km, n0, k0, p.N, p.K, tid);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldmatrix_x4(a[mi], &As[wm + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int ni = 0; ni < 4; ni += 2) {
+                uint32_t r[4];
+                ldmatrix_x4(r, &Bs[wn + ni * 8 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
+                b[ni][0] = r[0];
+                b[ni][1] = r[1];
+                b[ni + 1][0] = r[2];
+                b[ni + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = m0 + wm + mi * 16 + (lane >> 2) + (q >> 1) * 8;
+                const int c = n0 + wn + ni * 8 + (lane & 3) * 2 + (q & 1);
+                if (r >= p.M || c >= p.N) continue;
+                const float v = acc[mi][ni][q];
+                if (EPI == EPI_HIDDEN) {
+                    const float pre = v + p.bias[c];
+                    p.P_out[(long long)r * p.ldp + c] = __float2bfloat16(pre);
+                    p.Cb[(long long)r * p.ldc + c] = __float2bfloat16(gelu_f(pre));
+                } else if (EPI == EPI_OUT) {
+                    p.Cf[(long long)r * p.ldc + c] = v + p.bias[c];
+                } else if (EPI == EPI_DGELU) {
+                    const float pre = __bfloat162float(p.P_in[(long long)r * p.ldp + c]);
+                    p.Cb[(long long)r * p.ldc + c] = __float2bfloat16(v * gelu_grad_f(pre));
+                } else {
+                    p.Cf[(long long)r * p.ldc + c] = v;
+                }
+            }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+// normalised BF16 features X[s][slot] from FP64 rows z[s][row]
+__global__ void k_features(const double *__restrict__ z, long long zstride, const uint8_t *mask,
+                           const int *__restrict__ src, const float *__restrict__ mu,
+                           const float *__restrict__ sd, int FS, int S, bf16 *X) {
+    const long long n = (long long)S * FS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / FS;
+        const int f = (int)(i - s * FS);
+        const int r = src[f];
+        float v = 0.f;
+        if (r >= 0 && (!mask || mask[s * zstride + r]))
+            v = (float)((z[s * zstride + r] - (double)mu[f]) / (double)sd[f]);
+        X[i] = __float2bfloat16(v);
+    }
+}
+
+// per-slot statistics over samples (FP64 sums): feature slots read z rows,
+// output slots read the state
+__global__ void k_moments_rows(const double *__restrict__ z, long long zstride, const int *src,
+                               int FS, int S, double *sum, double *sum2) {
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < FS; f += gridDim.x * blockDim.x) {
+        const int r = src[f];
+        if (r < 0) continue;
+        double a = 0, b = 0;
+        for (int s = 0; s < S; ++s) {
+            const double v = z[(long long)s * zstride + r];
+            a += v;
+            b += v * v;
+        }
+        sum[f] += a;
+        sum2[f] += b;
+    }
+}
+
+// state (internal numbering) -> per-slot values: code = ibus * 2 + isT
+__device__ __forceinline__ double state_at(const double *xV, const double *xT, long long s, int N,
+                                           int code) {
+    const int ib = code >> 1;
+    return (code & 1) ? xT[s * N + ib] : xV[s * N + ib];
+}
+// magnitude outputs are learned relative to the bus's own voltage-magnitude
+// measurement (skip[o] = its row, -1 for angles and padding)
+__device__ __forceinline__ double skip_value(const double *z, long long zstride, const uint8_t *mask,
+                                             long long s, int row, double fallback) {
+    if (row < 0) return 0.0;
+    if (mask && !mask[s * zstride + row]) return fallback;
+    return z[s * zstride + row];
+}
+__global__ void k_moments_out(const double *__restrict__ xV, const double *__restrict__ xT, int N,
+                              const int *dst, const int *skip, const double *__restrict__ z,
+                              long long zstride, int OS, int S, double *sum, double *sum2) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < OS; o += gridDim.x * blockDim.x) {
+        const int code = dst[o];
+        if (code < 0) continue;
+        double a = 0, b = 0;
+        for (int s = 0; s < S; ++s) {
+            const double v = state_at(xV, xT, s, N, code) - skip_value(z, zstride, nullptr, s, skip[o], 0.0);
+            a += v;
+            b += v * v;
+        }
+        sum[o] += a;
+        sum2[o] += b;
+    }
+}
+__global__ void k_targets(const double *__restrict__ xV, const double *__restrict__ xT, int N,
+                          const int *dst, const int *skip, const double *__restrict__ z,
+                          long long zstride, const float *mu, const float *sd, int OS, int S, float *T) {
+    const long long n = (long long)S * OS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / OS;
+        const int o = (int)(i - s * OS);
+        const int code = dst[o];
+        if (code < 0) {
+            T[i] = 0.f;
+            continue;
+        }
+        const double v = state_at(xV, xT, s, N, code) - skip_value(z, zstride, nullptr, s, skip[o], 0.0);
+        T[i] = (float)((v - (double)mu[o]) / (double)sd[o]);
+    }
+}
+__global__ void k_finish_moments(const double *sum, const double *sum2, double n, int F, float *mu,
+                                 float *sd) {
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+        const double m = sum[f] / n;
+        const double var = fmax(sum2[f] / n - m * m, 0.0);
+        mu[f] = (float)m;
+        sd[f] = (float)fmax(sqrt(var), 1e-6);
+    }
+}
+
+// gather training rows of a batch
+__global__ void k_gather_batch(const bf16 *__restrict__ Xall, const float *__restrict__ Tall,
+                               const int *__restrict__ idx, int B, int FS, int OS, bf16 *X, float *T) {
+    const long long nx = (long long)B * (FS / 8);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nx;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / (FS / 8);
+        const long long c = i - b * (FS / 8);
+        ((uint4 *)X)[i] = ((const uint4 *)Xall)[(long long)idx[b] * (FS / 8) + c];
+    }
+    const long long nt = (long long)B * OS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / OS;
+        T[i] = Tall[(long long)idx[b] * OS + (i - b * OS)];
+    }
+}
+
+// MSE per area (mean over batch and real outputs) and its gradient in BF16
+__global__ void k_mse(const float *__restrict__ Y, const float *__restrict__ T,
+                      const float *__restrict__ scale, int B, int OS, bf16 *dY, float *dYf,
+                      double *loss) {
+    __shared__ double red[32];
+    double acc = 0;
+    const long long n = (long long)B * OS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(i % OS);
+        const float sc = scale[o];   // 1 / (B * d_out of the slot's area), 0 for padding
+        const float d = Y[i] - T[i];
+        const float g = 2.f * d * sc;
+        dY[i] = __float2bfloat16(g);
+        dYf[i] = g;
+        acc += (double)d * d * sc;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        atomicAdd(loss, t);
+    }
+}
+
+// bias gradients: column sums over the batch, scattered to the parameter
+// offsets (colmap[c] = index into grad, -1 for padding)
+template <class T>
+__global__ void k_colsum(const T *__restrict__ G, int B, int C, const long long *__restrict__ colmap,
+                         float *grad) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const long long dst = colmap[c];
+        if (dst < 0) continue;
+        float s = 0.f;
+        for (int b = 0; b < B; ++b) s += (float)G[(long long)b * C + c];
+        grad[dst] = s;
+    }
+}
+
+__global__ void k_adamw(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                        const float *__restrict__ g, bf16 *__restrict__ w16, long long n, float lr,
+                        float b1, float b2, float eps, float wd, float bc1, float bc2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float wi = w[i] * (1.f - lr * wd);
+        wi -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = wi;
+        w16[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ a, bf16 *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+// uniform(-a, a) initialisation from a counter-based generator (splitmix64)
+__global__ void k_init_uniform(float *w, long long off, long long n, float a, unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(off + i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float u = (float)((z >> 40) * (1.0 / 16777216.0));
+        w[off + i] = a * (2.f * u - 1.f);
+    }
+}
+
+// network output (normalised) -> state in internal numbering
+__global__ void k_apply(const float *__restrict__ Y, const int *__restrict__ dst,
+                        const int *__restrict__ skip, const double *__restrict__ z, long long zstride,
+                        const uint8_t *mask, const float *__restrict__ zmu,
+                        const float *__restrict__ mu, const float *__restrict__ sd, int OS, int S,
+                        int N, int slack_ibus, double *xV, double *xT) {
+    const long long n = (long long)S * OS;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / OS;
+        const int o = (int)(i - s * OS);
+        const int code = dst[o];
+        if (code < 0) continue;
+        const int ib = code >> 1;
+        const double base = skip[o] < 0 ? 0.0 : skip_value(z, zstride, mask, s, skip[o], (double)zmu[o]);
+        const double v = base + (double)Y[i] * (double)sd[o] + (double)mu[o];
+        if (code & 1) xT[s * N + ib] = ib == slack_ibus ? 0.0 : v;
+        else xV[s * N + ib] = v;
+    }
+}
+
+// per snapshot keep the start with the lower objective
+__global__ void k_pick_start(const double *Jl, const double *Jf, const double *xV2, const double *xT2,
+                             double *xV, double *xT, int N, int S, int *picked) {
+    const long long n = (long long)S * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / N;
+        const bool learned = Jl[s] < Jf[s];
+        if (learned) {
+            xV[i] = xV2[i];
+            xT[i] = xT2[i];
+        }
+        if (i - s * N == 0) picked[s] = learned ? 1 : 0;
+    }
+}
+
+inline int grid_for(long long n, int threads = 256) {
+    long long g = (n + threads - 1) / threads;
+    return (int)std::min<long long>(std::max<long long>(g, 1), 4096);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// model state
+// ---------------------------------------------------------------------------
+struct AreaNet {
+    int d_in, d_in_pad, d_out, d_out_pad;
+    long long w_off[4], b_off[4];
+    int fbase, obase;
+};
+
+struct Workspace {
+    int B = 0;
+    DevBuf<bf16> X, H, P, dA;   // [B][FS], [3][B][K*Hd] activations, pre-activations, grads
+    DevBuf<float> Y, T, dYf, scale;
+    DevBuf<bf16> dY;
+    DevBuf<GemmProb> fwd[4], bwdw[4], bwdd[3];
+    DevBuf<long long> colmap[4];
+    DevBuf<double> loss;
+};
+
+struct WarmStart {
+    int K = 0, Hd = 512, FS = 0, OS = 0, N = 0;
+    long long n_params = 0;
+    std::vector<AreaNet> nets;
+    std::vector<int> feat_src_h, out_dst_h, out_skip_h, out_skipfeat_h;
+    DevBuf<float> master, mom1, mom2, grad, feat_mu, feat_sd, out_mu, out_sd, skip_mu;
+    DevBuf<bf16> w16;
+    DevBuf<int> feat_src, out_dst, out_skip;
+    Workspace infer, train;
+    DevBuf<double> Jl, Jf;
+    DevBuf<int> picked;
+    long long steps = 0;
+    bool ready = false;
+    int slack_ibus = -1;
+};
+
+void destroy_warmstart(WarmStart *w) { delete w; }
+
+namespace {
+
+// layout of the per-area networks over the handle's areas
+int build_layout(mase_handle *h, WarmStart &W, int hidden) {
+    const mase::Setup &S = h->S;
+    W.K = S.K;
+    W.Hd = hidden;
+    W.N = S.N;
+    W.slack_ibus = S.ibus_of_bus[S.slack];
+    W.nets.resize(S.K);
+    long long off = 0;
+    int fb = 0, ob = 0, ibus0 = 0;
+    W.feat_src_h.clear();
+    W.out_dst_h.clear();
+    W.out_skip_h.clear();
+    W.out_skipfeat_h.clear();
+    for (int k = 0; k < S.K; ++k) {
+        const mase::AreaSetup &A = S.areas[k];
+        AreaNet &n = W.nets[k];
+        n.d_in = 3 * A.n_own + 2 * A.n_ends;
+        n.d_in_pad = pad8(n.d_in);
+        n.d_out = 2 * A.n_own;
+        n.d_out_pad = pad8(n.d_out);
+        const int din[4] = {n.d_in_pad, hidden, hidden, hidden};
+        const int dout[4] = {hidden, hidden, hidden, n.d_out_pad};
+        for (int l = 0; l < 4; ++l) {
+            n.w_off[l] = off;
+            off += (long long)din[l] * dout[l];
+            n.b_off[l] = off;
+            off += dout[l];
+        }
+        n.fbase = fb;
+        n.obase = ob;
+        for (int r = 0; r < n.d_in_pad; ++r) W.feat_src_h.push_back(r < n.d_in ? S.zrow_base[k] + r : -1);
+        for (int o = 0; o < n.d_out_pad; ++o) {
+            int code = -1, skip = -1;
+            if (o < A.n_own) {
+                code = (ibus0 + o) * 2;
+                skip = S.zrow_base[k] + o;        // the bus's voltage-magnitude row
+            } else if (o < 2 * A.n_own) {
+                code = (ibus0 + o - A.n_own) * 2 + 1;
+            }
+            W.out_dst_h.push_back(code);
+            W.out_skip_h.push_back(skip);
+            W.out_skipfeat_h.push_back(skip < 0 ? -1 : fb + o);   // its feature slot (mean for masked rows)
+        }
+        fb += n.d_in_pad;
+        ob += n.d_out_pad;
+        ibus0 += A.n_own;
+    }
+    W.FS = fb;
+    W.OS = ob;
+    W.n_params = off;
+    cudaStream_t st = h->stream;
+    WK(W.master.alloc(off));
+    WK(W.mom1.alloc(off));
+    WK(W.mom2.alloc(off));
+    WK(W.grad.alloc(off));
+    WK(W.w16.alloc(off));
+    WK(W.feat_src.upload(W.feat_src_h, st));
+    WK(W.out_dst.upload(W.out_dst_h, st));
+    WK(W.out_skip.upload(W.out_skip_h, st));
+    WK(W.skip_mu.alloc(W.OS));
+    WK(W.feat_mu.alloc(W.FS));
+    WK(W.feat_sd.alloc(W.FS));
+    WK(W.out_mu.alloc(W.OS));
+    WK(W.out_sd.alloc(W.OS));
+    WK(cudaMemsetAsync(W.mom1.p, 0, off * sizeof(float), st));
+    WK(cudaMemsetAsync(W.mom2.p, 0, off * sizeof(float), st));
+    WK(cudaMemsetAsync(W.grad.p, 0, off * sizeof(float), st));
+    return MASE_OK;
+}
+
+int init_weights(mase_handle *h, WarmStart &W, unsigned long long seed) {
+    cudaStream_t st = h->stream;
+    WK(cudaMemsetAsync(W.master.p, 0, W.n_params * sizeof(float), st));
+    for (int k = 0; k < W.K; ++k) {
+        const AreaNet &n = W.nets[k];
+        const int din[4] = {n.d_in_pad, W.Hd, W.Hd, W.Hd};
+        const int dout[4] = {W.Hd, W.Hd, W.Hd, n.d_out_pad};
+        for (int l = 0; l < 4; ++l) {
+            const int fan_in = l == 0 ? n.d_in : W.Hd;
+            const long long cnt = (long long)din[l] * dout[l];
+            k_init_uniform<<<grid_for(cnt), 256, 0, st>>>(W.master.p, n.w_off[l], cnt,
+                                                         1.0f / std::sqrt((float)fan_in), seed);
+        }
+    }
+    k_to_bf16<<<grid_for(W.n_params), 256, 0, st>>>(W.master.p, W.w16.p, W.n_params);
+    WK(cudaGetLastError());
+    return MASE_OK;
+}
+
+// mean of each magnitude output's skip row (used where the row is masked)
+__global__ void k_skip_means(const int *__restrict__ skipfeat, const float *__restrict__ feat_mu,
+                             int OS, float *skip_mu) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < OS; o += gridDim.x * blockDim.x)
+        skip_mu[o] = skipfeat[o] < 0 ? 0.f : feat_mu[skipfeat[o]];
+}
+int set_skip_means(mase_handle *h, WarmStart &W) {
+    DevBuf<int> sf;
+    WK(sf.upload(W.out_skipfeat_h, h->stream));
+    k_skip_means<<<grid_for(W.OS), 256, 0, h->stream>>>(sf.p, W.feat_mu.p, W.OS, W.skip_mu.p);
+    WK(cudaStreamSynchronize(h->stream));
+    return MASE_OK;
+}
+
+// GEMM descriptors of one workspace (pointers are fixed once allocated)
+int build_workspace(mase_handle *h, WarmStart &W, Workspace &ws, int B, bool training) {
+    if (ws.B == B) return MASE_OK;
+    cudaStream_t st = h->stream;
+    const int K = W.K, Hd = W.Hd;
+    const long long HB = (long long)K * Hd;
+    ws.B = B;
+    WK(ws.X.alloc((long long)B * W.FS));
+    WK(ws.H.alloc(3 * B * HB));
+    WK(ws.P.alloc(3 * B * HB));
+    WK(ws.Y.alloc((long long)B * W.OS));
+    WK(ws.loss.alloc(1));
+    if (training) {
+        WK(ws.dA.alloc(3 * B * HB));
+        WK(ws.T.alloc((long long)B * W.OS));
+        WK(ws.dYf.alloc((long long)B * W.OS));
+        WK(ws.dY.alloc((long long)B * W.OS));
+        std::vector<float> scale(W.OS, 0.f);
+        for (int k = 0; k < K; ++k)
+            for (int o = 0; o < W.nets[k].d_out; ++o)
+                scale[W.nets[k].obase + o] = 1.0f / ((float)B * (float)W.nets[k].d_out);
+        WK(ws.scale.upload(scale, st));
+    }
+    auto Hl = [&](int l) { return ws.H.p + (long long)l * B * HB; };
+    auto Pl = [&](int l) { return ws.P.p + (long long)l * B * HB; };
+    auto dAl = [&](int l) { return ws.dA.p + (long long)l * B * HB; };
+    for (int l = 0; l < 4; ++l) {
+        std::vector<GemmProb> f(K);
+        for (int k = 0; k < K; ++k) {
+            const AreaNet &n = W.nets[k];
+            GemmProb &g = f[k];
+            std::memset(&g, 0, sizeof(g));
+            g.M = B;
+            g.a_km = 1;
+            g.b_km = 1;
+            if (l == 0) {
+                g.A = ws.X.p + n.fbase;
+                g.lda = W.FS;
+                g.K = n.d_in_pad;
+            } else {
+                g.A = Hl(l - 1) + (long long)k * Hd;
+                g.lda = HB;
+                g.K = Hd;
+            }
+            g.B = W.w16.p + n.w_off[l];
+            g.ldb = g.K;
+            g.bias = W.master.p + n.b_off[l];
+            if (l < 3) {
+                g.N = Hd;
+                g.Cb = Hl(l) + (long long)k * Hd;
+                g.ldc = HB;
+                g.P_out = Pl(l) + (long long)k * Hd;
+                g.ldp = HB;
+            } else {
+                g.N = n.d_out_pad;
+                g.Cf = ws.Y.p + n.obase;
+                g.ldc = W.OS;
+            }
+        }
+        WK(ws.fwd[l].upload(f, st));
+    }
+    if (training) {
+        for (int l = 0; l < 4; ++l) {
+            // dW_l = dA_l^T * input_l  (M = out, N = in, K = B)
+            std::vector<GemmProb> f(K);
+            std::vector<long long> cm;
+            for (int k = 0; k < K; ++k) {
+                const AreaNet &n = W.nets[k];
+                GemmProb &g = f[k];
+                std::memset(&g, 0, sizeof(g));
+                g.K = B;
+                g.a_km = 0;
+                g.b_km = 0;
+                if (l == 3) {
+                    g.A = ws.dY.p + n.obase;
+                    g.lda = W.OS;
+                    g.M = n.d_out_pad;
+                } else {
+                    g.A = dAl(l) + (long long)k * Hd;
+                    g.lda = HB;
+                    g.M = Hd;
+                }
+                if (l == 0) {
+                    g.B = ws.X.p + n.fbase;
+                    g.ldb = W.FS;
+                    g.N = n.d_in_pad;
+                } else {
+                    g.B = Hl(l - 1) + (long long)k * Hd;
+                    g.ldb = HB;
+                    g.N = Hd;
+                }
+                g.Cf = W.grad.p + n.w_off[l];
+                g.ldc = g.N;
+            }
+            WK(ws.bwdw[l].upload(f, st));
+            // bias-gradient column maps
+            if (l == 3) {
+                cm.assign(W.OS, -1);
+                for (int k = 0; k < K; ++k)
+                    for (int o = 0; o < W.nets[k].d_out_pad; ++o) cm[W.nets[k].obase + o] = W.nets[k].b_off[3] + o;
+            } else {
+                cm.assign(HB, -1);
+                for (int k = 0; k < K; ++k)
+                    for (int j = 0; j < Hd; ++j) cm[(long long)k * Hd + j] = W.nets[k].b_off[l] + j;
+            }
+            WK(ws.colmap[l].upload(cm, st));
+        }
+        for (int l = 1; l < 4; ++l) {
+            // dA_{l-1} = (dA_l * W_l) .* gelu'(P_{l-1})  (M = B, N = in, K = out)
+            std::vector<GemmProb> f(K);
+            for (int k = 0; k < K; ++k) {
+                const AreaNet &n = W.nets[k];
+                GemmProb &g = f[k];
+                std::memset(&g, 0, sizeof(g));
+                g.M = B;
+                g.N = Hd;
+                g.a_km = 1;
+                g.b_km = 0;
+                if (l == 3) {
+                    g.A = ws.dY.p + n.obase;
+                    g.lda = W.OS;
+                    g.K = n.d_out_pad;
+                } else {
+                    g.A = dAl(l) + (long long)k * Hd;
+                    g.lda = HB;
+                    g.K = Hd;
+                }
+                g.B = W.w16.p + n.w_off[l];
+                g.ldb = Hd;
+                g.Cb = dAl(l - 1) + (long long)k * Hd;
+                g.ldc = HB;
+                g.P_in = Pl(l - 1) + (long long)k * Hd;
+                g.ldp = HB;
+            }
+            WK(ws.bwdd[l - 1].upload(f, st));
+        }
+    }
+    return MASE_OK;
+}
+
+int max_dim(const WarmStart &W, int l, bool out_dim) {
+    int m = 0;
+    for (const AreaNet &n : W.nets) {
+        if (out_dim) m = std::max(m, l < 3 ? W.Hd : n.d_out_pad);
+        else m = std::max(m, l == 0 ? n.d_in_pad : W.Hd);
+    }
+    return m;
+}
+
+// forward pass of every area's network on the workspace's features
+void forward(mase_handle *h, WarmStart &W, Workspace &ws, int *launches) {
+    cudaStream_t st = h->stream;
+    for (int l = 0; l < 4; ++l) {
+        const int nmax = max_dim(W, l, true);
+        dim3 grid((nmax + TB - 1) / TB, (ws.B + TB - 1) / TB, W.K);
+        if (l < 3) k_gemm_bf16<EPI_HIDDEN><<<grid, 128, 0, st>>>(ws.fwd[l].p);
+        else k_gemm_bf16<EPI_OUT><<<grid, 128, 0, st>>>(ws.fwd[l].p);
+        if (launches) ++*launches;
+    }
+}
+
+void backward(mase_handle *h, WarmStart &W, Workspace &ws) {
+    cudaStream_t st = h->stream;
+    const int B = ws.B, HB = W.K * W.Hd;
+    for (int l = 3; l >= 0; --l) {
+        const int mmax = l == 3 ? max_dim(W, 3, true) : W.Hd;
+        const int nmax = max_dim(W, l, false);
+        dim3 gw((nmax + TB - 1) / TB, (mmax + TB - 1) / TB, W.K);
+        k_gemm_bf16<EPI_GRAD><<<gw, 128, 0, st>>>(ws.bwdw[l].p);
+        if (l == 3) k_colsum<float><<<grid_for(W.OS), 256, 0, st>>>(ws.dYf.p, B, W.OS, ws.colmap[3].p, W.grad.p);
+        else k_colsum<bf16><<<grid_for(HB), 256, 0, st>>>(ws.dA.p + (long long)l * B * HB, B, HB, ws.colmap[l].p, W.grad.p);
+        if (l > 0) {
+            dim3 gd((W.Hd + TB - 1) / TB, (B + TB - 1) / TB, W.K);
+            k_gemm_bf16<EPI_DGELU><<<gd, 128, 0, st>>>(ws.bwdd[l - 1].p);
+        }
+    }
+}
+
+// moments and normalised features/targets of a chunk of internal-layout data
+int ingest_chunk(mase_handle *h, WarmStart &W, const double *z_can, const double *x_can, int n,
+                 bool host, DevBuf<double> &zc, DevBuf<double> &zi, DevBuf<double> &xc,
+                 DevBuf<double> &xv, DevBuf<double> &xt) {
+    cudaStream_t st = h->stream;
+    const int M = h->S.m, N = h->S.N;
+    const double *zsrc = z_can, *xsrc = x_can;
+    if (host) {
+        WK(cudaMemcpyAsync(zc.p, z_can, (size_t)n * M * sizeof(double), cudaMemcpyHostToDevice, st));
+        WK(cudaMemcpyAsync(xc.p, x_can, (size_t)n * 2 * N * sizeof(double), cudaMemcpyHostToDevice, st));
+        zsrc = zc.p;
+        xsrc = xc.p;
+    }
+    mase_dev::k_gather_rows<<<1024, 256, 0, st>>>(zsrc, zi.p, h->zperm.p, M, n);
+    mase_dev::k_state_in<<<1024, 256, 0, st>>>(xsrc, xv.p, xt.p, h->bus_of_ibus.p, N, n, 0);
+    WK(cudaGetLastError());
+    return MASE_OK;
+}
+
+}  // namespace
+
+// learned start for the handle's current batch, judged against the flat start
+int learned_start(mase_handle *h, int *launches) {
+    WarmStart *W = h->ws;
+    if (!W || !W->ready) return fail(MASE_ENOTREADY, "no trained warm-start model");
+    cudaStream_t st = h->stream;
+    const int S = h->n_snap, N = h->S.N, M = h->S.m;
+    int rc = build_workspace(h, *W, W->infer, S, false);
+    if (rc != MASE_OK) return rc;
+    if (!W->Jl.p) {
+        WK(W->Jl.alloc(S));
+        WK(W->Jf.alloc(S));
+        WK(W->picked.alloc(S));
+        WK(h->xV2.alloc((size_t)S * N));
+        WK(h->xT2.alloc((size_t)S * N));
+    }
+    Workspace &ws = W->infer;
+    k_features<<<grid_for((long long)S * W->FS), 256, 0, st>>>(
+        h->z_int.p, M, h->has_mask ? h->mask_int.p : nullptr, W->feat_src.p, W->feat_mu.p,
+        W->feat_sd.p, W->FS, S, ws.X.p);
+    ++*launches;
+    forward(h, *W, ws, launches);
+    // learned state into (xV2, xT2) on top of a flat start (slack angle 0)
+    mase_dev::k_state_in<<<1024, 256, 0, st>>>(nullptr, h->xV2.p, h->xT2.p, h->bus_of_ibus.p, N, S, 1);
+    k_apply<<<grid_for((long long)S * W->OS), 256, 0, st>>>(
+        ws.Y.p, W->out_dst.p, W->out_skip.p, h->z_int.p, M, h->has_mask ? h->mask_int.p : nullptr,
+        W->skip_mu.p, W->out_mu.p, W->out_sd.p, W->OS, S, N, W->slack_ibus, h->xV2.p, h->xT2.p);
+    launches[0] += 2;
+    WK(cudaGetLastError());
+    // objective at both starts with the area kernel in objective mode
+    WK(cudaMemsetAsync(W->Jl.p, 0, S * sizeof(double), st));
+    WK(cudaMemsetAsync(W->Jf.p, 0, S * sizeof(double), st));
+    launch_objective(h, h->xV2.p, h->xT2.p, W->Jl.p, launches);
+    launch_objective(h, h->xV.p, h->xT.p, W->Jf.p, launches);
+    k_pick_start<<<grid_for((long long)S * N), 256, 0, st>>>(W->Jl.p, W->Jf.p, h->xV2.p, h->xT2.p,
+                                                            h->xV.p, h->xT.p, N, S, W->picked.p);
+    launches[0] += 1;
+    WK(cudaGetLastError());
+    return MASE_OK;
+}
+
+}  // namespace mase_internal
+
+using namespace mase_internal;
+
+extern "C" {
+
+void mase_warmstart_default_options(mase_warmstart_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->hidden = 512;
+    o->epochs = 20;
+    o->batch = 256;
+    o->lr = 1e-3f;
+    o->weight_decay = 1e-4f;
+    o->seed = 1;
+}
+
+int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32_t n,
+                         const mase_warmstart_options *opt_in, double *final_loss) {
+    if (!h || !z || !x) return fail(MASE_EINVAL, "null argument");
+    mase_warmstart_options opt;
+    if (opt_in) opt = *opt_in;
+    else mase_warmstart_default_options(&opt);
+    if (n < 8 || opt.batch < 8 || opt.batch % 8 || opt.batch > n || opt.epochs < 1 ||
+        opt.hidden < 8 || opt.hidden % 8 || !(opt.lr > 0.f))
+        return fail(MASE_EINVAL, "bad warm-start training arguments");
+    if (cudaSetDevice(h->opt.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice");
+    cudaStream_t st = h->stream;
+    WK(cudaEventRecord(h->ev_in, h->user_stream));
+    WK(cudaStreamWaitEvent(st, h->ev_in, 0));
+    if (h->ws) {
+        delete h->ws;
+        h->ws = nullptr;
+    }
+    WarmStart *W = new WarmStart();
+    h->ws = W;
+    int rc = build_layout(h, *W, opt.hidden);
+    if (rc != MASE_OK) return rc;
+    rc = init_weights(h, *W, opt.seed);
+    if (rc != MASE_OK) return rc;
+    const int M = h->S.m, N = h->S.N;
+    const bool zh = !is_device_pointer(z), xh = !is_device_pointer(x);
+    const bool host = zh || xh;
+    if (zh != xh) return fail(MASE_EINVAL, "z and x must both be host or both device pointers");
+    // pass 1: moments of features and targets; pass 2: normalised training set
+    const int chunk = 512;
+    DevBuf<double> zc, zi, xc, xv, xt, fs1, fs2, os1, os2;
+    WK(zi.alloc((size_t)chunk * M));
+    WK(xv.alloc((size_t)chunk * N));
+    WK(xt.alloc((size_t)chunk * N));
+    if (host) {
+        WK(zc.alloc((size_t)chunk * M));
+        WK(xc.alloc((size_t)chunk * 2 * N));
+    }
+    WK(fs1.alloc(W->FS));
+    WK(fs2.alloc(W->FS));
+    WK(os1.alloc(W->OS));
+    WK(os2.alloc(W->OS));
+    WK(cudaMemsetAsync(fs1.p, 0, W->FS * sizeof(double), st));
+    WK(cudaMemsetAsync(fs2.p, 0, W->FS * sizeof(double), st));
+    WK(cudaMemsetAsync(os1.p, 0, W->OS * sizeof(double), st));
+    WK(cudaMemsetAsync(os2.p, 0, W->OS * sizeof(double), st));
+    for (int s0 = 0; s0 < n; s0 += chunk) {
+        const int c = std::min(chunk, n - s0);
+        rc = ingest_chunk(h, *W, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        if (rc != MASE_OK) return rc;
+        k_moments_rows<<<grid_for(W->FS), 256, 0, st>>>(zi.p, M, W->feat_src.p, W->FS, c, fs1.p, fs2.p);
+        k_moments_out<<<grid_for(W->OS), 256, 0, st>>>(xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M,
+                                                      W->OS, c, os1.p, os2.p);
+    }
+    k_finish_moments<<<grid_for(W->FS), 256, 0, st>>>(fs1.p, fs2.p, (double)n, W->FS, W->feat_mu.p, W->feat_sd.p);
+    k_finish_moments<<<grid_for(W->OS), 256, 0, st>>>(os1.p, os2.p, (double)n, W->OS, W->out_mu.p, W->out_sd.p);
+    rc = set_skip_means(h, *W);
+    if (rc != MASE_OK) return rc;
+    DevBuf<bf16> Xall;
+    DevBuf<float> Tall;
+    WK(Xall.alloc((size_t)n * W->FS));
+    WK(Tall.alloc((size_t)n * W->OS));
+    for (int s0 = 0; s0 < n; s0 += chunk) {
+        const int c = std::min(chunk, n - s0);
+        rc = ingest_chunk(h, *W, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        if (rc != MASE_OK) return rc;
+        k_features<<<grid_for((long long)c * W->FS), 256, 0, st>>>(
+            zi.p, M, nullptr, W->feat_src.p, W->feat_mu.p, W->feat_sd.p, W->FS, c,
+            Xall.p + (size_t)s0 * W->FS);
+        k_targets<<<grid_for((long long)c * W->OS), 256, 0, st>>>(
+            xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M, W->out_mu.p, W->out_sd.p, W->OS, c,
+            Tall.p + (size_t)s0 * W->OS);
+    }
+    WK(cudaGetLastError());
+    // training
+    rc = build_workspace(h, *W, W->train, opt.batch, true);
+    if (rc != MASE_OK) return rc;
+    Workspace &ws = W->train;
+    const int steps_per_epoch = n / opt.batch;
+    const long long total = (long long)steps_per_epoch * opt.epochs;
+    std::mt19937_64 rng(opt.seed);
+    std::vector<int> perm(n);
+    DevBuf<int> idx;
+    WK(idx.alloc((size_t)opt.batch * steps_per_epoch));
+    double last_epoch_loss = 0;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    long long t = 0;
+    for (int ep = 0; ep < opt.epochs; ++ep) {
+        std::iota(perm.begin(), perm.end(), 0);
+        std::shuffle(perm.begin(), perm.end(), rng);
+        WK(cudaMemcpyAsync(idx.p, perm.data(), (size_t)opt.batch * steps_per_epoch * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+        WK(cudaMemsetAsync(ws.loss.p, 0, sizeof(double), st));
+        for (int sp = 0; sp < steps_per_epoch; ++sp) {
+            ++t;
+            k_gather_batch<<<grid_for((long long)opt.batch * W->FS / 8), 256, 0, st>>>(
+                Xall.p, Tall.p, idx.p + (size_t)sp * opt.batch, opt.batch, W->FS, W->OS, ws.X.p, ws.T.p);
+            forward(h, *W, ws, nullptr);
+            k_mse<<<grid_for((long long)opt.batch * W->OS), 256, 0, st>>>(
+                ws.Y.p, ws.T.p, ws.scale.p, opt.batch, W->OS, ws.dY.p, ws.dYf.p, ws.loss.p);
+            backward(h, *W, ws);
+            // cosine decay of the learning rate to 5 % of its peak
+            const double frac = (double)(t - 1) / std::max<long long>(1, total - 1);
+            const float lr = opt.lr * (float)(0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac)));
+            const float bc1 = 1.f - std::pow(b1, (float)t), bc2 = 1.f - std::pow(b2, (float)t);
+            k_adamw<<<grid_for(W->n_params), 256, 0, st>>>(W->master.p, W->mom1.p, W->mom2.p, W->grad.p,
+                                                          W->w16.p, W->n_params, lr, b1, b2, eps,
+                                                          opt.weight_decay, bc1, bc2);
+        }
+        double l = 0;
+        WK(cudaMemcpyAsync(&l, ws.loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        WK(cudaStreamSynchronize(st));
+        last_epoch_loss = l / std::max(1, steps_per_epoch) / W->K;
+    }
+    WK(cudaGetLastError());
+    W->steps = t;
+    W->ready = true;
+    if (final_loss) *final_loss = last_epoch_loss;
+    WK(cudaStreamSynchronize(st));
+    WK(cudaEventRecord(h->ev_out, st));
+    WK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+    return MASE_OK;
+}
+
+int mase_warmstart_predict(mase_handle *h, double *x_out) {
+    if (!h || !x_out) return fail(MASE_EINVAL, "null argument");
+    WarmStart *W = h->ws;
+    if (!W || !W->ready) return fail(MASE_ENOTREADY, "no trained warm-start model");
+    if (!h->has_z) return fail(MASE_ENOTREADY, "no measurements set");
+    if (cudaSetDevice(h->opt.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice");
+    cudaStream_t st = h->stream;
+    const int S = h->n_snap, N = h->S.N, M = h->S.m;
+    WK(cudaEventRecord(h->ev_in, h->user_stream));
+    WK(cudaStreamWaitEvent(st, h->ev_in, 0));
+    int rc = build_workspace(h, *W, W->infer, S, false);
+    if (rc != MASE_OK) return rc;
+    if (!h->xV2.p) {
+        WK(h->xV2.alloc((size_t)S * N));
+        WK(h->xT2.alloc((size_t)S * N));
+    }
+    Workspace &ws = W->infer;
+    k_features<<<grid_for((long long)S * W->FS), 256, 0, st>>>(
+        h->z_int.p, M, h->has_mask ? h->mask_int.p : nullptr, W->feat_src.p, W->feat_mu.p,
+        W->feat_sd.p, W->FS, S, ws.X.p);
+    forward(h, *W, ws, nullptr);
+    mase_dev::k_state_in<<<1024, 256, 0, st>>>(nullptr, h->xV2.p, h->xT2.p, h->bus_of_ibus.p, N, S, 1);
+    k_apply<<<grid_for((long long)S * W->OS), 256, 0, st>>>(
+        ws.Y.p, W->out_dst.p, W->out_skip.p, h->z_int.p, M, h->has_mask ? h->mask_int.p : nullptr,
+        W->skip_mu.p, W->out_mu.p, W->out_sd.p, W->OS, S, N, W->slack_ibus, h->xV2.p, h->xT2.p);
+    const bool dev = is_device_pointer(x_out);
+    double *dst = dev ? x_out : h->xbuf.p;
+    mase_dev::k_state_out<<<1024, 256, 0, st>>>(dst, h->xV2.p, h->xT2.p, h->bus_of_ibus.p, N, S);
+    if (!dev)
+        WK(cudaMemcpyAsync(x_out, h->xbuf.p, (size_t)2 * N * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    WK(cudaGetLastError());
+    WK(cudaStreamSynchronize(st));
+    WK(cudaEventRecord(h->ev_out, st));
+    WK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+    return MASE_OK;
+}
+
+// file: "MASEWS01", int32 K, hidden, FS, OS, per area (d_in, d_out), int64 n_params,
+// float feat_mu[FS], feat_sd[FS], out_mu[OS], out_sd[OS], master[n_params]
+int mase_warmstart_save(const mase_handle *hc, const char *path) {
+    mase_handle *h = const_cast<mase_handle *>(hc);
+    if (!h || !path) return fail(MASE_EINVAL, "null argument");
+    WarmStart *W = h->ws;
+    if (!W || !W->ready) return fail(MASE_ENOTREADY, "no trained warm-start model");
+    cudaStream_t st = h->stream;
+    std::vector<float> fm(W->FS), fsd(W->FS), om(W->OS), osd(W->OS), w(W->n_params);
+    WK(cudaMemcpyAsync(fm.data(), W->feat_mu.p, W->FS * 4, cudaMemcpyDeviceToHost, st));
+    WK(cudaMemcpyAsync(fsd.data(), W->feat_sd.p, W->FS * 4, cudaMemcpyDeviceToHost, st));
+    WK(cudaMemcpyAsync(om.data(), W->out_mu.p, W->OS * 4, cudaMemcpyDeviceToHost, st));
+    WK(cudaMemcpyAsync(osd.data(), W->out_sd.p, W->OS * 4, cudaMemcpyDeviceToHost, st));
+    WK(cudaMemcpyAsync(w.data(), W->master.p, W->n_params * 4, cudaMemcpyDeviceToHost, st));
+    WK(cudaStreamSynchronize(st));
+    std::ofstream f(path, std::ios::binary);
+    if (!f) return fail(MASE_EINVAL, std::string("cannot write ") + path);
+    f.write("MASEWS01", 8);
+    const int32_t hdr[4] = {W->K, W->Hd, W->FS, W->OS};
+    f.write((const char *)hdr, sizeof(hdr));
+    for (const AreaNet &n : W->nets) {
+        const int32_t d[2] = {n.d_in, n.d_out};
+        f.write((const char *)d, sizeof(d));
+    }
+    const int64_t np = W->n_params;
+    f.write((const char *)&np, sizeof(np));
+    f.write((const char *)fm.data(), fm.size() * 4);
+    f.write((const char *)fsd.data(), fsd.size() * 4);
+    f.write((const char *)om.data(), om.size() * 4);
+    f.write((const char *)osd.data(), osd.size() * 4);
+    f.write((const char *)w.data(), w.size() * 4);
+    return f ? MASE_OK : fail(MASE_EINVAL, "write failed");
+}
+
+int mase_warmstart_load(mase_handle *h, const char *path) {
+    if (!h || !path) return fail(MASE_EINVAL, "null argument");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(MASE_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    f.read(magic, 8);
+    if (!f || std::memcmp(magic, "MASEWS01", 8)) return fail(MASE_EINVAL, "not a warm-start file");
+    int32_t hdr[4];
+    f.read((char *)hdr, sizeof(hdr));
+    if (cudaSetDevice(h->opt.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice");
+    WarmStart *W = new WarmStart();
+    int rc = build_layout(h, *W, hdr[1]);
+    if (rc != MASE_OK) {
+        delete W;
+        return rc;
+    }
+    bool ok = hdr[0] == W->K && hdr[2] == W->FS && hdr[3] == W->OS;
+    for (const AreaNet &n : W->nets) {
+        int32_t d[2];
+        f.read((char *)d, sizeof(d));
+        ok = ok && d[0] == n.d_in && d[1] == n.d_out;
+    }
+    int64_t np = 0;
+    f.read((char *)&np, sizeof(np));
+    if (!f || !ok || np != W->n_params) {
+        delete W;
+        return fail(MASE_EINVAL, "warm-start file does not match this network and partition");
+    }
+    std::vector<float> fm(W->FS), fsd(W->FS), om(W->OS), osd(W->OS), w(np);
+    f.read((char *)fm.data(), fm.size() * 4);
+    f.read((char *)fsd.data(), fsd.size() * 4);
+    f.read((char *)om.data(), om.size() * 4);
+    f.read((char *)osd.data(), osd.size() * 4);
+    f.read((char *)w.data(), w.size() * 4);
+    if (!f) {
+        delete W;
+        return fail(MASE_EINVAL, "truncated warm-start file");
+    }
+    cudaStream_t st = h->stream;
+    WK(cudaMemcpyAsync(W->feat_mu.p, fm.data(), W->FS * 4, cudaMemcpyHostToDevice, st));
+    WK(cudaMemcpyAsync(W->feat_sd.p, fsd.data(), W->FS * 4, cudaMemcpyHostToDevice, st));
+    WK(cudaMemcpyAsync(W->out_mu.p, om.data(), W->OS * 4, cudaMemcpyHostToDevice, st));
+    WK(cudaMemcpyAsync(W->out_sd.p, osd.data(), W->OS * 4, cudaMemcpyHostToDevice, st));
+    WK(cudaMemcpyAsync(W->master.p, w.data(), np * 4, cudaMemcpyHostToDevice, st));
+    k_to_bf16<<<grid_for(np), 256, 0, st>>>(W->master.p, W->w16.p, np);
+    WK(cudaStreamSynchronize(st));
+    rc = set_skip_means(h, *W);
+    if (rc != MASE_OK) {
+        delete W;
+        return rc;
+    }
+    W->ready = true;
+    delete h->ws;
+    h->ws = W;
+    return MASE_OK;
+}
+
+// One forward + backward pass of a single MLP (Linear-GELU ... Linear, MSE)
+// with the same kernels as training; used to check the gradients.
+int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const float *params,
+                   const float *X, const float *T, float *loss, float *grads) {
+    if (!dims || !params || !X || !T || !grads || n_layers != 4 || batch < 1)
+        return fail(MASE_EINVAL, "mase_mlp_check expects 4 layers (3 hidden) and a batch >= 1");
+    const int Hd = dims[1];
+    if (dims[2] != Hd || dims[3] != Hd || Hd % 8) return fail(MASE_EINVAL, "hidden widths must be equal multiples of 8");
+    // a one-area warm start with the given widths
+    mase_handle tmp;
+    tmp.stream = nullptr;
+    WarmStart W;
+    W.K = 1;
+    W.Hd = Hd;
+    AreaNet n;
+    n.d_in = dims[0];
+    n.d_in_pad = pad8(dims[0]);
+    n.d_out = dims[4];
+    n.d_out_pad = pad8(dims[4]);
+    n.fbase = 0;
+    n.obase = 0;
+    const int din[4] = {n.d_in_pad, Hd, Hd, Hd}, dout[4] = {Hd, Hd, Hd, n.d_out_pad};
+    const int rin[4] = {n.d_in, Hd, Hd, Hd}, rout[4] = {Hd, Hd, Hd, n.d_out};
+    long long off = 0;
+    for (int l = 0; l < 4; ++l) {
+        n.w_off[l] = off;
+        off += (long long)din[l] * dout[l];
+        n.b_off[l] = off;
+        off += dout[l];
+    }
+    W.nets.push_back(n);
+    W.FS = n.d_in_pad;
+    W.OS = n.d_out_pad;
+    W.n_params = off;
+    const int B = pad8(batch);
+    // padded parameters from the packed input (W_l [out][in] then b_l per layer)
+    std::vector<float> P(off, 0.f);
+    long long src = 0;
+    for (int l = 0; l < 4; ++l) {
+        for (int o = 0; o < rout[l]; ++o)
+            for (int i = 0; i < rin[l]; ++i) P[n.w_off[l] + (long long)o * din[l] + i] = params[src++];
+        for (int o = 0; o < rout[l]; ++o) P[n.b_off[l] + o] = params[src++];
+    }
+    WK(W.master.upload(P, nullptr));
+    WK(W.w16.alloc(off));
+    WK(W.grad.alloc(off));
+    WK(cudaMemset(W.grad.p, 0, off * 4));
+    k_to_bf16<<<grid_for(off), 256>>>(W.master.p, W.w16.p, off);
+    int rc = build_workspace(&tmp, W, W.train, B, true);
+    if (rc != MASE_OK) return rc;
+    Workspace &ws = W.train;
+    // the loss is over the real batch rows only: padded rows get zero scale
+    std::vector<float> scale(W.OS, 0.f);
+    for (int o = 0; o < n.d_out; ++o) scale[o] = 1.0f / ((float)batch * n.d_out);
+    std::vector<bf16> Xh((size_t)B * W.FS, __float2bfloat16(0.f));
+    std::vector<float> Th((size_t)B * W.OS, 0.f);
+    for (int b = 0; b < batch; ++b) {
+        for (int i = 0; i < n.d_in; ++i) Xh[(size_t)b * W.FS + i] = __float2bfloat16(X[(size_t)b * n.d_in + i]);
+        for (int o = 0; o < n.d_out; ++o) Th[(size_t)b * W.OS + o] = T[(size_t)b * n.d_out + o];
+    }
+    WK(cudaMemcpy(ws.X.p, Xh.data(), Xh.size() * sizeof(bf16), cudaMemcpyHostToDevice));
+    WK(cudaMemcpy(ws.T.p, Th.data(), Th.size() * 4, cudaMemcpyHostToDevice));
+    WK(cudaMemcpy(ws.scale.p, scale.data(), scale.size() * 4, cudaMemcpyHostToDevice));
+    WK(cudaMemset(ws.loss.p, 0, sizeof(double)));
+    // padded batch rows must contribute no gradient: zero their targets' scale via
+    // the rows of dY (k_mse uses per-column scale, so mask rows afterwards)
+    forward(&tmp, W, ws, nullptr);
+    k_mse<<<grid_for((long long)B * W.OS), 256>>>(ws.Y.p, ws.T.p, ws.scale.p, B, W.OS, ws.dY.p, ws.dYf.p, ws.loss.p);
+    if (B > batch) {
+        WK(cudaMemset(ws.dY.p + (size_t)batch * W.OS, 0, (size_t)(B - batch) * W.OS * sizeof(bf16)));
+        WK(cudaMemset(ws.dYf.p + (size_t)batch * W.OS, 0, (size_t)(B - batch) * W.OS * sizeof(float)));
+    }
+    backward(&tmp, W, ws);
+    WK(cudaGetLastError());
+    WK(cudaDeviceSynchronize());
+    double l = 0;
+    WK(cudaMemcpy(&l, ws.loss.p, sizeof(double), cudaMemcpyDeviceToHost));
+    if (B > batch) {
+        // the padded rows added (0 - 0)^2 * scale = 0 only if their outputs are 0;
+        // recompute the loss over the real rows from Y
+        std::vector<float> Y((size_t)B * W.OS);
+        WK(cudaMemcpy(Y.data(), ws.Y.p, Y.size() * 4, cudaMemcpyDeviceToHost));
+        l = 0;
+        for (int b = 0; b < batch; ++b)
+            for (int o = 0; o < n.d_out; ++o) {
+                const double d = Y[(size_t)b * W.OS + o] - T[(size_t)b * n.d_out + o];
+                l += d * d / ((double)batch * n.d_out);
+            }
+    }
+    if (loss) *loss = (float)l;
+    std::vector<float> G(off);
+    WK(cudaMemcpy(G.data(), W.grad.p, off * 4, cudaMemcpyDeviceToHost));
+    long long dst = 0;
+    for (int ll = 0; ll < 4; ++ll) {
+        for (int o = 0; o < rout[ll]; ++o)
+            for (int i = 0; i < rin[ll]; ++i) grads[dst++] = G[n.w_off[ll] + (long long)o * din[ll] + i];
+        for (int o = 0; o < rout[ll]; ++o) grads[dst++] = G[n.b_off[ll] + o];
+    }
+    return MASE_OK;
+}
+
+}  // extern "C"

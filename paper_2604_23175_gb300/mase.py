@@ -53,6 +53,11 @@ class Stats(C.Structure):
                 ("steps", C.c_int32)]
 
 
+class WarmstartOptions(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("epochs", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
+
+
 class Info(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_area", C.c_int32),
                 ("n_snap", C.c_int32), ("n_meas", C.c_int32), ("n_state", C.c_int32),
@@ -103,6 +108,15 @@ def load() -> C.CDLL:
         "mase_selfcheck": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.c_uint64, _f64p]),
         "mase_analyze_error": (C.c_char_p, []),
         "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "mase_warmstart_default_options": (None, [C.POINTER(WarmstartOptions)]),
+        "mase_warmstart_train": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int32,
+                                           C.POINTER(WarmstartOptions), C.POINTER(C.c_double)]),
+        "mase_warmstart_predict": (C.c_int, [H, C.c_void_p]),
+        "mase_warmstart_save": (C.c_int, [H, C.c_char_p]),
+        "mase_warmstart_load": (C.c_int, [H, C.c_char_p]),
+        "mase_mlp_check": (C.c_int, [_i32p, C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -270,9 +284,56 @@ class Estimator:
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
 
+    # ---- learned warm start
+    def warmstart_train(self, z, x, epochs=20, batch=256, lr=1e-3, weight_decay=1e-4, hidden=512,
+                        seed=1) -> float:
+        """Train the per-area networks on (z, x) pairs; returns the last-epoch loss."""
+        o = WarmstartOptions()
+        self.lib.mase_warmstart_default_options(C.byref(o))
+        o.hidden, o.epochs, o.batch, o.lr, o.weight_decay, o.seed = hidden, epochs, batch, lr, weight_decay, seed
+        loss = C.c_double()
+        n = int(z.shape[0])
+        rc = self.lib.mase_warmstart_train(self.h, _ptr(z), _ptr(x), n, C.byref(o), C.byref(loss))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+        return loss.value
+
+    def warmstart_predict(self, x_out):
+        rc = self.lib.mase_warmstart_predict(self.h, _ptr(x_out))
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def warmstart_save(self, path: str):
+        rc = self.lib.mase_warmstart_save(self.h, path.encode())
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
+    def warmstart_load(self, path: str):
+        rc = self.lib.mase_warmstart_load(self.h, path.encode())
+        if rc != MASE_OK:
+            raise MaseError(rc, _last_error())
+
     def info(self) -> dict:
         inf = Info()
         rc = self.lib.mase_get_info(self.h, C.byref(inf))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
         return inf.as_dict()
+
+
+def mlp_check(dims, params, X, T):
+    """One forward/backward pass of a single warm-start network with the
+    library's training kernels: returns (loss, grads) (FP32)."""
+    lib = load()
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    Xa = np.ascontiguousarray(X, dtype=np.float32)
+    Ta = np.ascontiguousarray(T, dtype=np.float32)
+    g = np.zeros_like(p)
+    loss = C.c_float()
+    fp = C.POINTER(C.c_float)
+    rc = lib.mase_mlp_check(d.ctypes.data_as(_i32p), len(d) - 1, int(Xa.shape[0]), p.ctypes.data_as(fp),
+                            Xa.ctypes.data_as(fp), Ta.ctypes.data_as(fp), C.byref(loss), g.ctypes.data_as(fp))
+    if rc != MASE_OK:
+        raise MaseError(rc, _last_error())
+    return loss.value, g
