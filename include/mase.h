@@ -61,6 +61,7 @@ extern "C" {
 #define MASE_SNAP_MAX_ITER      1
 #define MASE_SNAP_NOT_SPD       2
 #define MASE_SNAP_NONFINITE     3
+#define MASE_SNAP_DEVICE        4   /* a bounded device-side wait gave up      */
 
 /* precision modes */
 #define MASE_FP64   0   /* every step in FP64 (the plain comparator)               */

@@ -46,6 +46,9 @@ struct AreaDev {
     int in_smem;
     int off_g, off_y, off_bus, off_end, off_inj, off_self, off_st;   // dynamic smem byte offsets
     int smem_bytes;
+    int back_smem;          // 1: the back-substitution stages the factor in shared memory
+    int back_off_st;        // its byte offset there (after the rhs)
+    int back_smem_bytes;
     long long fac_base;     // element offset of (area, snapshot 0) in the factor buffer
     int fac_stride;         // elements per snapshot (= store_total)
     long long c_base;       // interior forward-solved rhs, stride n_int
@@ -82,7 +85,7 @@ struct State {
     const double *W;             // [M] 1/sigma^2
     const uint8_t *mask;         // [S][M] or null
     int *active;                 // [S]
-    int *err;                    // [S] bit 1: non-SPD pivot, bit 2: non-finite
+    int *err;                    // [S] bit 1: non-SPD pivot, bit 2: non-finite, bit 4: a bounded wait gave up
     double *J;                   // [S]
     unsigned long long *maxstep; // [S] bit pattern of max |dx| (non-negative double)
 };
@@ -127,6 +130,47 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return t;
 }
 
+// Bulk copy (TMA, non-tensor cp.async.bulk) of `bytes` bytes from global to
+// this block's shared memory, completed on an mbarrier.  Both addresses must
+// be 16-byte aligned and bytes a multiple of 16 (<= 1 MiB).  Must be reached
+// by every thread of the block.  The wait is bounded: on give-up it returns
+// false after waiting (again bounded) for the copy still in flight.
+__device__ __forceinline__ bool bulk_to_smem(void *dst, const void *src, unsigned bytes,
+                                             unsigned long long *mbar) {
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(mbar);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+            "l"(src), "r"(bytes), "r"(mb)
+            : "memory");
+    }
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(0u)
+            : "memory");
+    if (!done) {
+        for (int it = 0; it < (1 << 22) && !done; ++it)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(mb), "r"(0u)
+                : "memory");
+        return false;
+    }
+    return true;
+}
+
 // P and Q leaving bus i into a branch towards j (pi model, Sec. 2.1 bus-branch
 // formulation), from cos/sin of both angles: theta_ij = theta_i - theta_j.
 struct EndFlow {
@@ -155,6 +199,22 @@ __device__ __forceinline__ EndFlow end_flow(double Vi, double Vj, double ci, dou
 // ---------------------------------------------------------------------------
 // supernodal factorisation with trailing Schur block + forward solve
 // ---------------------------------------------------------------------------
+
+// Factor storage accessors.  Every supernode panel lies wholly in one
+// memory, so a panel base is resolved once; update targets are resolved per
+// entry.
+template <class RG>
+struct FlatStore {   // one contiguous block (shared or global memory)
+    RG *p;
+    __device__ __forceinline__ RG *at(int off) const { return p + off; }
+};
+template <class RG>
+struct SplitStore {  // entries [split, ...) in shared memory, the rest in global memory
+    RG *g;
+    RG *sm;
+    int split;
+    __device__ __forceinline__ RG *at(int off) const { return off >= split ? sm + (off - split) : g + off; }
+};
 
 // Diagonal block of a supernode panel (w <= WB <= 32 columns), by one warp:
 // lane r holds row r, column values are broadcast by shuffles; then the
@@ -255,8 +315,8 @@ __device__ __forceinline__ void panel_rows_any(RG *P, int w, int ld, int r0, int
 // Updates of one unit (NJ target columns j0 .. j0+NJ of a supernode's row
 // set) for the rows i >= j0 held by this lane; RHS adds the rhs update of the
 // supernode (carried by the unit with j0 = 0).
-template <class RG, class RS, int NJ, bool RHS>
-__device__ __forceinline__ void unit_rows(RG *st, RS *y, const RG *Ps, const int *relp,
+template <class RG, class RS, int NJ, bool RHS, class ST>
+__device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, const int *relp,
                                           const int *rws, const RS *yc, int w, int ld, int j0,
                                           const int4 cb4, int tg0, int lane) {
     const int R = ld - w;
@@ -276,7 +336,7 @@ __device__ __forceinline__ void unit_rows(RG *st, RS *y, const RG *Ps, const int
         }
 #pragma unroll
         for (int k = 0; k < NJ; ++k)
-            if (ir >= j0 + k) atomicAdd(st + cb[k] + tg, -v[k]);
+            if (ir >= j0 + k) atomicAdd(st.at(cb[k] + tg), -v[k]);
         if (RHS) atomicAdd(y + rws[ir], -vr);
     }
 }
@@ -285,8 +345,8 @@ __device__ __forceinline__ void unit_rows(RG *st, RS *y, const RG *Ps, const int
 // level.  Updates of ancestors -- including the trailing Schur block and the
 // boundary part of the rhs -- are scattered with atomics through the
 // relative-index maps.  Must be called by every thread of the block.
-template <class RG, class RS>
-__device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, bool do_factor,
+template <class RG, class RS, class ST>
+__device__ void factor_forward(const FacDev &F, const Tables &T, const ST &st, RS *y, bool do_factor,
                                int *err) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
@@ -302,7 +362,7 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
             const int w = T.sn_w[s];
-            diag_block_any<RG, RS>(st + T.sn_off[s], w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
+            diag_block_any<RG, RS>(st.at(T.sn_off[s]), w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
                                    lane, err);
         }
         __syncthreads();
@@ -315,7 +375,7 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
             if (k1 > k0) {
                 for (int k = k0 + warp; k < k1; k += nw) {
                     const int4 r = crec[k];
-                    panel_rows_any<RG>(st + r.x, r.y, r.z, r.w, lane);
+                    panel_rows_any<RG>(st.at(r.x), r.y, r.z, r.w, lane);
                 }
                 __syncthreads();
             }
@@ -358,24 +418,24 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
                     nnb = urec[3 * unn + 1];
                     nnc = urec[3 * unn + 2];
                 }
-                const RG *Ps = st + ra.x;
+                const RG *Ps = st.at(ra.x);
                 const int *relp = rel + ra.y;
                 const int *rws = rows + ra.z;
                 const RS *yc = y + ra.w;
                 const int w = rb.x, ld = rb.y, j0 = rb.z, nj = rb.w;
                 if (j0 == 0) {
                     switch (nj) {
-                        case 1: unit_rows<RG, RS, 1, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 2: unit_rows<RG, RS, 2, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 3: unit_rows<RG, RS, 3, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        default: unit_rows<RG, RS, 4, true>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 1: unit_rows<RG, RS, 1, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 2: unit_rows<RG, RS, 2, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 3: unit_rows<RG, RS, 3, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        default: unit_rows<RG, RS, 4, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
                     }
                 } else {
                     switch (nj) {
-                        case 1: unit_rows<RG, RS, 1, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 2: unit_rows<RG, RS, 2, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 3: unit_rows<RG, RS, 3, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        default: unit_rows<RG, RS, 4, false>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 1: unit_rows<RG, RS, 1, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 2: unit_rows<RG, RS, 2, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        case 3: unit_rows<RG, RS, 3, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
+                        default: unit_rows<RG, RS, 4, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
                     }
                 }
                 ra = na;
@@ -391,7 +451,7 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
             for (int i = a + warp; i < e; i += nw) {
                 const int s = F.sn_base + sn_order[i];
                 const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
-                const RG *Ps = st + T.sn_off[s] + w;
+                const RG *Ps = st.at(T.sn_off[s]) + w;
                 const int rb = F.rows_base + T.sn_rows[s];
                 const RS *yc = y + T.sn_c0[s];
                 for (int ir = lane; ir < R; ir += 32) {
@@ -408,8 +468,8 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, RG *st, RS *y, 
 // Backward solve L^T x = y over the internal supernodes, top level first.
 // y[n_int..] must hold the (already known) boundary unknowns; on return
 // y[0..n_int) holds the interior solution (Eq. backsub).
-template <class RG, class RS>
-__device__ void back_solve(const FacDev &F, const Tables &T, const RG *st, RS *y) {
+template <class RG, class RS, class ST>
+__device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
@@ -418,7 +478,7 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const RG *st, RS *y
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
             const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R, c0 = T.sn_c0[s];
-            const RG *P = st + T.sn_off[s];
+            const RG *P = st.at(T.sn_off[s]);
             const int *rows = T.rows + F.rows_base + T.sn_rows[s];
             for (int c = 0; c < w; ++c) {
                 RS acc = RS(0);
@@ -645,7 +705,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     for (int i = tid; i < nv; i += nt) y[i] = RS(g[i]);
     __syncthreads();
     // ---- Schur-mode factorisation (Sec. 4.3): leaves S_b and b_hat in the trailing block
-    factor_forward<RG, RS>(A.F, T, st, y, true, &s_err);
+    factor_forward<RG, RS>(A.F, T, FlatStore<RG>{st}, y, true, &s_err);
     // ---- outputs
     if (A.in_smem) {
         RG *dst = fac + A.fac_base + (long long)s * A.fac_stride;
@@ -672,6 +732,8 @@ struct BndDev {
     const int *rhs_beg, *rhs_area, *rhs_lv;
     const int *bvar_ibus, *bvar_isT;
     long long stride;     // storage elements per snapshot
+    int split;            // storage entries from here on live in shared memory
+    int smem_off_st;      // their byte offset in dynamic shared memory
 };
 
 template <class RG, class RS>
@@ -689,7 +751,8 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
     double *x = bhat + nG;
     double *r = x + nG;
     RS *y = (RS *)(r + nG);
-    RG *st = bst + (long long)s * B.stride;
+    // the top of the elimination tree (most updates) in shared memory, the rest in global
+    const SplitStore<RG> st{bst + (long long)s * B.stride, (RG *)(smem + B.smem_off_st), B.split};
     RG *Am = bA + (long long)s * B.stride;
     if (tid == 0) s_err = 0;
     for (int P = tid; P < B.F.store_total; P += nt) {
@@ -698,7 +761,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
             const AreaDev &A = areas[B.asm_area[i]];
             v += fac[A.fac_base + (long long)s * A.fac_stride + B.asm_off[i]];
         }
-        st[P] = v;
+        *st.at(P) = v;
         Am[P] = v;
     }
     for (int gi = tid; gi < nG; gi += nt) {
@@ -791,13 +854,26 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
     if (!X.active[s]) return;
     const AreaDev A = areas[k];
     const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ unsigned long long mbar;
     RS *y = (RS *)smem;
+    const RG *fsrc = fac + A.fac_base + (long long)s * A.fac_stride;
+    const RG *fst = fsrc;
+    if (A.back_smem) {
+        // stage the interior factor into shared memory with one bulk copy
+        RG *dst = (RG *)(smem + A.back_off_st);
+        const unsigned bytes = (unsigned)(((A.F.store_int * sizeof(RG)) + 15) & ~size_t(15));
+        if (!bulk_to_smem(dst, fsrc, bytes, &mbar)) {
+            if (tid == 0) atomicOr(X.err + s, 4);
+            return;
+        }
+        fst = dst;
+    }
     const RS *c = cvec + A.c_base + (long long)s * A.F.n_int;
     for (int i = tid; i < A.F.n_int; i += nt) y[i] = c[i];
     for (int lv = tid; lv < A.F.n_bnd; lv += nt)
         y[A.F.n_int + lv] = RS(dxG[(long long)s * n_gamma + T.ebnd[A.ebnd_base + lv]]);
     __syncthreads();
-    back_solve<RG, RS>(A.F, T, fac + A.fac_base + (long long)s * A.fac_stride, y);
+    back_solve<RG, RS>(A.F, T, FlatStore<const RG>{fst}, y);
     double mx = 0.0;
     bool bad = false;
     for (int q = tid; q < A.nb_int; q += nt) {
@@ -847,7 +923,8 @@ __global__ void k_finalize(State X, int *iters, int *status, double *laststep,
             laststep[s] = m;
             const int e = X.err[s];
             int st = -1;
-            if (e & 1) st = 2;                       // MASE_SNAP_NOT_SPD
+            if (e & 4) st = 4;                       // MASE_SNAP_DEVICE (bounded wait gave up)
+            else if (e & 1) st = 2;                  // MASE_SNAP_NOT_SPD
             else if ((e & 2) || !isfinite(m)) st = 3; // MASE_SNAP_NONFINITE
             else if (m < tol) st = 0;                 // MASE_SNAP_CONVERGED
             else if (it >= max_iter) st = 1;          // MASE_SNAP_MAX_ITER

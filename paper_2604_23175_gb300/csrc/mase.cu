@@ -189,7 +189,7 @@ int enqueue_step(mase_handle *h, int *launches) {
         ++*launches;
     } else {
         for (int k = 0; k < K; ++k) {
-            size_t sm = (size_t)(h->areas_h[k].F.n_int + h->areas_h[k].F.n_bnd) * sizeof(RS);
+            const size_t sm = (size_t)h->areas_h[k].back_smem_bytes;
             k_back<RG, RS><<<S, kBackThreads, sm, st>>>(h->d_areas.p, h->T, X, nullptr, k, fac, cv, h->dxG.p,
                                              h->bnd.n_gamma);
             ++*launches;
@@ -296,10 +296,19 @@ int build(mase_handle *h) {
         if (o > (size_t)h->smem_limit)
             return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large for shared memory");
         max_local = std::max(max_local, (size_t)d.smem_bytes);
-        max_back = std::max(max_back, (size_t)nv * sizeof(RS));
+        {
+            // back-substitution: rhs, then (when it fits) the staged interior factor
+            const size_t yb = ((size_t)nv * sizeof(RS) + 15) & ~size_t(15);
+            const size_t fb = ((size_t)A.F.store_int * sizeof(RG) + 15) & ~size_t(15);
+            d.back_off_st = (int)yb;
+            d.back_smem = (yb + fb <= (size_t)h->smem_limit) ? 1 : 0;
+            d.back_smem_bytes = (int)(d.back_smem ? yb + fb : yb);
+            max_back = std::max(max_back, (size_t)d.back_smem_bytes);
+        }
         d.fac_base = fac_off;
-        d.fac_stride = A.F.store_total;
-        fac_off += (long long)A.F.store_total * nS;
+        // instance bases stay 16-byte aligned for the bulk copies
+        d.fac_stride = (A.F.store_total + 3) & ~3;
+        fac_off += (long long)d.fac_stride * nS;
         d.c_base = c_off;
         c_off += (long long)A.n_int * nS;
         d.bh_base = bh_off;
@@ -326,9 +335,22 @@ int build(mase_handle *h) {
     bd.F = append_fac(H, B.F);
     bd.n_gamma = B.n_gamma;
     bd.stride = B.F.store_total;
-    h->smem_bnd = (size_t)B.n_gamma * (3 * sizeof(double) + sizeof(RS)) + 16;
-    if (h->smem_bnd > (size_t)h->smem_limit)
-        return set_err(MASE_EINVAL, "boundary system too large for shared-memory vectors");
+    {
+        // vectors first, then as much of the top of the boundary factor as fits
+        const size_t vec = (((size_t)B.n_gamma * (3 * sizeof(double) + sizeof(RS))) + 15) & ~size_t(15);
+        if (vec > (size_t)h->smem_limit)
+            return set_err(MASE_EINVAL, "boundary system too large for shared-memory vectors");
+        const long long room = ((long long)h->smem_limit - (long long)vec) / (long long)sizeof(RG);
+        int split = B.F.store_total;
+        for (int sn = 0; sn < B.F.nsn(); ++sn)
+            if ((long long)B.F.store_total - B.F.sn_off[sn] <= room) {
+                split = B.F.sn_off[sn];
+                break;
+            }
+        bd.split = split;
+        bd.smem_off_st = (int)vec;
+        h->smem_bnd = vec + (size_t)(B.F.store_total - split) * sizeof(RG);
+    }
     // instance list: areas by descending work, snapshots innermost
     std::vector<int> ord(K);
     for (int k = 0; k < K; ++k) ord[k] = k;
@@ -551,6 +573,7 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         if (status[s] == MASE_SNAP_MAX_ITER && ret == MASE_OK) ret = MASE_NOT_CONVERGED;
         if (status[s] == MASE_SNAP_NOT_SPD) ret = MASE_EUNOBSERVABLE;
         if (status[s] == MASE_SNAP_NONFINITE && ret != MASE_EUNOBSERVABLE) ret = MASE_ENONFINITE;
+        if (status[s] == MASE_SNAP_DEVICE) ret = MASE_EDEVICE;
     }
     if (stats) {
         for (int s = 0; s < nS; ++s) {
@@ -565,6 +588,7 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     if (ret == MASE_EUNOBSERVABLE) set_err(ret, "non-positive pivot in an area or boundary factor");
     if (ret == MASE_ENONFINITE) set_err(ret, "non-finite step");
+    if (ret == MASE_EDEVICE) set_err(ret, "a bounded device-side wait gave up");
     return ret;
 }
 

@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
         y[gi] = RS(v);
     }
     __syncthreads();
-    factor_forward<RG, RS>(B.F, T, st, y, true, &s_err);
-    back_solve<RG, RS>(B.F, T, st, y);
+    factor_forward<RG, RS>(B.F, T, FlatStore<RG>{st}, y, true, &s_err);
+    back_solve<RG, RS>(B.F, T, FlatStore<RG>{st}, y);
     for (int gi = tid; gi < nG; gi += nt) x[gi] = double(y[gi]);
     __syncthreads();
     for (int it = 0; it < refine; ++it) {
@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
         __syncthreads();
         for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
         __syncthreads();
-        factor_forward<RG, RS>(B.F, T, st, y, false, &s_err);
-        back_solve<RG, RS>(B.F, T, st, y);
+        factor_forward<RG, RS>(B.F, T, FlatStore<RG>{st}, y, false, &s_err);
+        back_solve<RG, RS>(B.F, T, FlatStore<RG>{st}, y);
         for (int gi = tid; gi < nG; gi += nt) x[gi] += double(y[gi]);
         __syncthreads();
     }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmase.so")
 
 MASE_OK, MASE_NOT_CONVERGED = 0, 1
 MASE_EINVAL, MASE_EUNOBSERVABLE, MASE_ENONFINITE, MASE_EDEVICE, MASE_ENOTREADY = -1, -2, -3, -4, -5
-SNAP_CONVERGED, SNAP_MAX_ITER, SNAP_NOT_SPD, SNAP_NONFINITE = 0, 1, 2, 3
+SNAP_CONVERGED, SNAP_MAX_ITER, SNAP_NOT_SPD, SNAP_NONFINITE, SNAP_DEVICE = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 START_FLAT, START_X0, START_LEARNED = 0, 1, 2
 PER_AREA, BATCHED = 0, 1
