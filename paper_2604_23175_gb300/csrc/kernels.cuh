@@ -46,9 +46,7 @@ struct AreaDev {
     int in_smem;
     int off_g, off_y, off_bus, off_end, off_inj, off_self, off_st;   // dynamic smem byte offsets
     int smem_bytes;
-    int back_smem;          // 1: the back-substitution stages the factor in shared memory
-    int back_off_st;        // its byte offset there (after the rhs)
-    int back_smem_bytes;
+    int back_smem_bytes;    // dynamic shared memory of the back-substitution (rhs)
     long long fac_base;     // element offset of (area, snapshot 0) in the factor buffer
     int fac_stride;         // elements per snapshot (= store_total)
     long long c_base;       // interior forward-solved rhs, stride n_int
@@ -128,47 +126,6 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     if (threadIdx.x == 0)
         for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
     return t;
-}
-
-// Bulk copy (TMA, non-tensor cp.async.bulk) of `bytes` bytes from global to
-// this block's shared memory, completed on an mbarrier.  Both addresses must
-// be 16-byte aligned and bytes a multiple of 16 (<= 1 MiB).  Must be reached
-// by every thread of the block.  The wait is bounded: on give-up it returns
-// false after waiting (again bounded) for the copy still in flight.
-__device__ __forceinline__ bool bulk_to_smem(void *dst, const void *src, unsigned bytes,
-                                             unsigned long long *mbar) {
-    const unsigned mb = (unsigned)__cvta_generic_to_shared(mbar);
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-            "l"(src), "r"(bytes), "r"(mb)
-            : "memory");
-    }
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mb), "r"(0u)
-            : "memory");
-    if (!done) {
-        for (int it = 0; it < (1 << 22) && !done; ++it)
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(mb), "r"(0u)
-                : "memory");
-        return false;
-    }
-    return true;
 }
 
 // P and Q leaving bus i into a branch towards j (pi model, Sec. 2.1 bus-branch
@@ -854,20 +811,10 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
     if (!X.active[s]) return;
     const AreaDev A = areas[k];
     const int tid = threadIdx.x, nt = blockDim.x;
-    __shared__ unsigned long long mbar;
     RS *y = (RS *)smem;
-    const RG *fsrc = fac + A.fac_base + (long long)s * A.fac_stride;
-    const RG *fst = fsrc;
-    if (A.back_smem) {
-        // stage the interior factor into shared memory with one bulk copy
-        RG *dst = (RG *)(smem + A.back_off_st);
-        const unsigned bytes = (unsigned)(((A.F.store_int * sizeof(RG)) + 15) & ~size_t(15));
-        if (!bulk_to_smem(dst, fsrc, bytes, &mbar)) {
-            if (tid == 0) atomicOr(X.err + s, 4);
-            return;
-        }
-        fst = dst;
-    }
+    // each factor entry is read once, straight from global memory: many small
+    // blocks per SM hide the latency better than staging the factor on chip
+    const RG *fst = fac + A.fac_base + (long long)s * A.fac_stride;
     const RS *c = cvec + A.c_base + (long long)s * A.F.n_int;
     for (int i = tid; i < A.F.n_int; i += nt) y[i] = c[i];
     for (int lv = tid; lv < A.F.n_bnd; lv += nt)

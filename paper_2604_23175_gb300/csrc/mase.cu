@@ -296,17 +296,10 @@ int build(mase_handle *h) {
         if (o > (size_t)h->smem_limit)
             return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large for shared memory");
         max_local = std::max(max_local, (size_t)d.smem_bytes);
-        {
-            // back-substitution: rhs, then (when it fits) the staged interior factor
-            const size_t yb = ((size_t)nv * sizeof(RS) + 15) & ~size_t(15);
-            const size_t fb = ((size_t)A.F.store_int * sizeof(RG) + 15) & ~size_t(15);
-            d.back_off_st = (int)yb;
-            d.back_smem = (yb + fb <= (size_t)h->smem_limit) ? 1 : 0;
-            d.back_smem_bytes = (int)(d.back_smem ? yb + fb : yb);
-            max_back = std::max(max_back, (size_t)d.back_smem_bytes);
-        }
+        d.back_smem_bytes = (int)(((size_t)nv * sizeof(RS) + 15) & ~size_t(15));
+        max_back = std::max(max_back, (size_t)d.back_smem_bytes);
         d.fac_base = fac_off;
-        // instance bases stay 16-byte aligned for the bulk copies
+        // instance bases stay 16-byte aligned
         d.fac_stride = (A.F.store_total + 3) & ~3;
         fac_off += (long long)d.fac_stride * nS;
         d.c_base = c_off;
