@@ -21,7 +21,7 @@ struct HostTables {
     std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
     std::vector<double> end_g, end_b, end_bh;
     std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
-    std::vector<int> unit_sn, unit_j, lev_units, unit_rec, item_rec, chunk_rec, lev_chunks;
+    std::vector<int> tasks, lev_tasks, item_rec, chunk_rec, lev_chunks;
 };
 
 template <class T>
@@ -89,10 +89,11 @@ struct mase_handle {
         t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
         t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
         t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
-        t_unit_sn, t_unit_j, t_lev_units, t_unit_rec, t_item_rec, t_chunk_rec, t_lev_chunks;
+        t_tasks, t_lev_tasks, t_item_rec, t_chunk_rec, t_lev_chunks;
     DevBuf<double> t_end_g, t_end_b, t_end_bh;
     DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,
-        b_bvar_isT;
+        b_bvar_isT, b_asm_str, b_rhs_str;
+    DevBuf<long long> b_asm_abs, b_rhs_abs;
     Tables T{};
     DevBuf<int2> d_inst;
     std::vector<int2> inst_h;

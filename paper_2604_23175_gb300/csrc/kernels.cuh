@@ -32,9 +32,11 @@ struct FacDev {
     int levoff_base;   // lev_off (nlev + 1 entries)
     int rows_base;     // rows / colbase / relbase
     int rel_base;      // rel
-    int unit_base;     // unit_sn / unit_j / unit_rec (12 ints per unit)
-    int levunit_base;  // lev_units (nlev + 1 entries)
-    int chunk_base;    // chunk_rec (4 ints per chunk)
+    int task_base;     // task_rec (16 ints per task)
+    int n_tasks;
+    int level_sched;   // 1: tasks grouped by level (lev_tasks), 0: dataflow order
+    int levtask_base;  // lev_tasks (3 nlev + 1 entries)
+    int chunk_base;    // chunk_rec (8 ints per chunk)
     int levchunk_base; // lev_chunks (nlev + 1 entries)
 };
 
@@ -64,10 +66,10 @@ struct Tables {
     const int *slot_q, *slot_ebeg, *slot_ecnt;
     const int *item_own, *item_uv, *item_pos;
     const int *ebnd;
-    const int *unit_sn, *unit_j, *lev_units;
-    const int4 *unit_rec;   // 3 int4 per unit
+    const int4 *task_rec;   // 4 int4 per factorisation task
+    const int *lev_tasks;   // level schedule: group boundaries of the task list
     const int4 *item_rec;   // 1 int4 per injection item
-    const int4 *chunk_rec;  // 1 int4 per 32-row panel chunk
+    const int4 *chunk_rec;  // 2 int4 per 32-row panel chunk
     const int *lev_chunks;
 };
 
@@ -189,7 +191,7 @@ __device__ void diag_block(RG *P, int w, int ld, RS *yc, bool do_factor, int lan
             if (c < w) {
                 RG d = __shfl_sync(FULL, a[c], c);
                 if (!(d > RG(0))) {
-                    if (lane == 0) *err = 1;
+                    if (lane == 0) atomicOr(err, 1);
                     d = RG(1);
                 }
                 // the diagonal entry is stored as its reciprocal 1/L_cc so that
@@ -250,6 +252,55 @@ __device__ void panel_rows(RG *P, int w, int ld, int r0, int lane) {
         if (c < w) P[(size_t)c * ld + row] = x[c];
 }
 
+// Diagonal block wider than 16 columns as a 2 x 2 block Cholesky: factor the
+// leading 16 columns, solve the rows 16..w-1 against them, update the trailing
+// block and its rhs, factor the trailing block.  No step holds more than 16
+// values per lane, so the tile stays in registers.
+template <class RG, class RS>
+__device__ void diag_block_wide(RG *P, int w, int ld, RS *yc, bool do_factor, int lane, int *err) {
+    constexpr int H = 16;
+    diag_block<RG, RS, H>(P, H, ld, yc, do_factor, lane, err);
+    __syncwarp();
+    const int r = H + lane;
+    const bool mine = lane < w - H;
+    if (do_factor) {
+        // L21 = A21 L11^-T for the rows H..w-1 of the block
+        RG x[H];
+#pragma unroll
+        for (int c = 0; c < H; ++c) x[c] = mine ? P[(size_t)c * ld + r] : RG(0);
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+            const RG *Lc = P + (size_t)c * ld;
+            x[c] *= Lc[c];
+#pragma unroll
+            for (int c2 = c + 1; c2 < H; ++c2) x[c2] -= x[c] * Lc[c2];
+        }
+        if (mine) {
+#pragma unroll
+            for (int c = 0; c < H; ++c) P[(size_t)c * ld + r] = x[c];
+        }
+        __syncwarp();
+        // A22 -= L21 L21^T (lower part): lane r updates its row
+        if (mine) {
+            for (int c2 = H; c2 <= r; ++c2) {
+                RG v = RG(0);
+#pragma unroll
+                for (int k = 0; k < H; ++k) v += x[k] * P[(size_t)k * ld + c2];
+                P[(size_t)c2 * ld + r] -= v;
+            }
+        }
+    }
+    // rhs of the trailing rows: y2 -= L21 y1
+    if (mine) {
+        RS v = RS(0);
+#pragma unroll
+        for (int k = 0; k < H; ++k) v += RS(P[(size_t)k * ld + r]) * yc[k];
+        yc[r] -= v;
+    }
+    __syncwarp();
+    diag_block<RG, RS, H>(P + (size_t)H * ld + H, w - H, ld, yc + H, do_factor, lane, err);
+}
+
 template <class RG, class RS>
 __device__ __forceinline__ void diag_block_any(RG *P, int w, int ld, RS *yc, bool do_factor,
                                                int lane, int *err) {
@@ -257,7 +308,7 @@ __device__ __forceinline__ void diag_block_any(RG *P, int w, int ld, RS *yc, boo
     else if (w <= 4) diag_block<RG, RS, 4>(P, w, ld, yc, do_factor, lane, err);
     else if (w <= 8) diag_block<RG, RS, 8>(P, w, ld, yc, do_factor, lane, err);
     else if (w <= 16) diag_block<RG, RS, 16>(P, w, ld, yc, do_factor, lane, err);
-    else diag_block<RG, RS, 32>(P, w, ld, yc, do_factor, lane, err);
+    else diag_block_wide<RG, RS>(P, w, ld, yc, do_factor, lane, err);
 }
 
 template <class RG>
@@ -269,153 +320,225 @@ __device__ __forceinline__ void panel_rows_any(RG *P, int w, int ld, int r0, int
     else panel_rows<RG, 32>(P, w, ld, r0, lane);
 }
 
-// Updates of one unit (NJ target columns j0 .. j0+NJ of a supernode's row
-// set) for the rows i >= j0 held by this lane; RHS adds the rhs update of the
-// supernode (carried by the unit with j0 = 0).
-template <class RG, class RS, int NJ, bool RHS, class ST>
-__device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, const int *relp,
+// Updates of one unit: NJ target columns j0 .. j0+NJ of a supernode's row set,
+// for the rows i >= j0.  A pass covers MC 32-row chunks (lane = row within a
+// chunk), so every target-column value loaded from shared memory serves MC
+// rows; rows i < rhs_end also update the rhs (the unit that starts a target
+// segment carries that segment's rows).  Index loads are issued up front.
+template <class RG, class RS, int NJ, int MC, class ST>
+__device__ __forceinline__ void unit_pass(const ST &st, RS *y, const RG *Ps, const int *relp,
                                           const int *rws, const RS *yc, int w, int ld, int j0,
-                                          const int4 cb4, int tg0, int lane) {
+                                          int rhs_end, const int (&cb)[4], int i0, int lane) {
     const int R = ld - w;
-    const int cb[4] = {cb4.x, cb4.y, cb4.z, cb4.w};
-    for (int ir = j0 + lane; ir < R; ir += 32) {
-        const int tg = ir < j0 + 32 ? tg0 : relp[ir];
-        RG v[NJ];
+    int ir[MC], tg[MC], rw[MC];
+    bool ok[MC], rh[MC];
 #pragma unroll
-        for (int k = 0; k < NJ; ++k) v[k] = RG(0);
-        RS vr = RS(0);
-        for (int c = 0; c < w; ++c) {
-            const RG li = Ps[(size_t)c * ld + ir];
-            const RG *lj = Ps + (size_t)c * ld + j0;
+    for (int m = 0; m < MC; ++m) {
+        ir[m] = i0 + 32 * m + lane;
+        ok[m] = ir[m] < R;
+        rh[m] = ir[m] < rhs_end;
+        tg[m] = ok[m] ? relp[ir[m]] : 0;
+        rw[m] = rh[m] ? rws[ir[m]] : 0;
+    }
+    const bool any_rhs = i0 < rhs_end;
+    RG v[MC][NJ];
+    RS vr[MC];
 #pragma unroll
-            for (int k = 0; k < NJ; ++k) v[k] += li * lj[k];
-            if (RHS) vr += RS(li) * yc[c];
+    for (int m = 0; m < MC; ++m) {
+        vr[m] = RS(0);
+#pragma unroll
+        for (int k = 0; k < NJ; ++k) v[m][k] = RG(0);
+    }
+    for (int c = 0; c < w; ++c) {
+        const RG *col = Ps + (size_t)c * ld;
+        RG lj[NJ];
+#pragma unroll
+        for (int k = 0; k < NJ; ++k) lj[k] = col[j0 + k];
+        const RS ycc = any_rhs ? yc[c] : RS(0);
+#pragma unroll
+        for (int m = 0; m < MC; ++m) {
+            const RG li = ok[m] ? col[ir[m]] : RG(0);
+#pragma unroll
+            for (int k = 0; k < NJ; ++k) v[m][k] += li * lj[k];
+            vr[m] += RS(li) * ycc;
         }
+    }
 #pragma unroll
-        for (int k = 0; k < NJ; ++k)
-            if (ir >= j0 + k) atomicAdd(st.at(cb[k] + tg), -v[k]);
-        if (RHS) atomicAdd(y + rws[ir], -vr);
+    for (int m = 0; m < MC; ++m) {
+        if (ok[m]) {
+#pragma unroll
+            for (int k = 0; k < NJ; ++k)
+                if (ir[m] >= j0 + k) atomicAdd(st.at(cb[k] + tg[m]), -v[m][k]);
+        }
+        if (rh[m]) atomicAdd(y + rw[m], -vr[m]);
     }
 }
 
-// Factor (optionally) and forward-solve the internal supernodes level by
-// level.  Updates of ancestors -- including the trailing Schur block and the
-// boundary part of the rhs -- are scattered with atomics through the
-// relative-index maps.  Must be called by every thread of the block.
+template <class RG, class RS, int NJ, class ST>
+__device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, const int *relp,
+                                          const int *rws, const RS *yc, int w, int ld, int j0,
+                                          int rhs_end, const int (&cb)[4], int lane) {
+    const int R = ld - w;
+    int i0 = j0;
+    for (; i0 + 64 < R; i0 += 96)
+        unit_pass<RG, RS, NJ, 3, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, i0, lane);
+    if (i0 + 32 < R)
+        unit_pass<RG, RS, NJ, 2, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, i0, lane);
+    else if (i0 < R)
+        unit_pass<RG, RS, NJ, 1, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, i0, lane);
+}
+
+// Task bodies are kept out of line so that each gets the whole register file
+// for its own tile (the 32-column diagonal block lives in 32 registers).
 template <class RG, class RS, class ST>
-__device__ void factor_forward(const FacDev &F, const Tables &T, const ST &st, RS *y, bool do_factor,
-                               int *err) {
+__device__ __noinline__ void task_diag(const ST st, int off, int w, int ld, RS *yc, int *err) {
+    diag_block_any<RG, RS>(st.at(off), w, ld, yc, true, threadIdx.x & 31, err);
+}
+template <class RG, class ST>
+__device__ __noinline__ void task_panel(const ST st, int off, int w, int ld, int r0) {
+    panel_rows_any<RG>(st.at(off), w, ld, r0, threadIdx.x & 31);
+}
+template <class RG, class RS, class ST>
+__device__ __noinline__ void task_unit(const ST st, RS *y, const int *rel, const int *rows,
+                                       const int4 q1, const int4 q2, const int4 q3) {
+    const int lane = threadIdx.x & 31;
+    const RG *Ps = st.at(q1.x);
+    const int *relp = rel + q1.y;
+    const int *rws = rows + q1.z;
+    const RS *yc = y + q1.w;
+    const int w = q2.x & 0xff, nj = q2.x >> 8, ld = q2.y & 0xffff, j0 = q2.y >> 16;
+    const int rhs_end = q2.z;
+    const int cb[4] = {q2.w, q3.x, q3.y, q3.z};
+    switch (nj) {
+        case 1: unit_rows<RG, RS, 1, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
+        case 2: unit_rows<RG, RS, 2, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
+        case 3: unit_rows<RG, RS, 3, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
+        default: unit_rows<RG, RS, 4, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
+    }
+}
+
+// Numeric factorisation + forward solve as a dataflow over the task list
+// (diagonal blocks, panel chunks, update units).  A free warp takes the next
+// task index from a shared counter, waits (bounded) until the task's counter
+// reaches its threshold, runs it and signals its own counter.  Tasks are in a
+// topological order, so the lowest unfinished task can always run.  Updates
+// of ancestors, of the trailing Schur block and of the rhs are scattered with
+// shared/global atomics through the relative-index maps.  ctr holds 2 nsn + 1
+// ints of shared memory.  Must be called by every thread of the block.
+template <class RG, class RS, class ST>
+__device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS *y, int *ctr,
+                             int *err) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int kWaitLimit = 1 << 22;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int nsn = F.nsn, ntask = F.n_tasks;
+    for (int i = tid; i <= 2 * nsn; i += nt) ctr[i] = 0;
+    __syncthreads();
+    const int4 *trec = T.task_rec + 4 * (long long)F.task_base;
+    const int *rel = T.rel + F.rel_base;
+    const int *rows = T.rows + F.rows_base;
+    int *next = ctr + 2 * nsn;
+    for (;;) {
+        // a warp takes the next task only when it is free, so a task on the
+        // critical path never queues behind a long one
+        int t = 0;
+        if (lane == 0) t = atomicAdd(next, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= ntask) break;
+        const int4 q0 = trec[4 * t], q1 = trec[4 * t + 1], q2 = trec[4 * t + 2], q3 = trec[4 * t + 3];
+        if (lane == 0 && q0.z > 0) {
+            const volatile int *c = ctr + q0.y;
+            int it = 0;
+            while (*c < q0.z) {
+                if (++it > kWaitLimit) {
+                    atomicOr(err, 4);
+                    break;
+                }
+                __nanosleep(32);
+            }
+            __threadfence_block();
+        }
+        __syncwarp();
+        const int type = q0.x >> 24;
+        if (type == 0) task_diag<RG, RS, ST>(st, q1.x, q1.y, q1.z, y + q1.w, err);
+        else if (type == 1) task_panel<RG, ST>(st, q1.x, q1.y, q1.z, q1.w);
+        else task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3);
+        __syncwarp();
+        if (lane == 0 && q0.w >= 0) {
+            __threadfence_block();
+            atomicAdd(ctr + q0.w, 1);
+        }
+    }
+    __syncthreads();
+}
+
+// The same factorisation with a level schedule: per level, the diagonal
+// blocks, then the panel chunks, then the update units, each group spread over
+// the warps and closed by a block barrier.  Suits factors whose top levels are
+// wide (the boundary system) better than the dataflow.
+template <class RG, class RS, class ST>
+__device__ void factor_levels(const FacDev &F, const Tables &T, const ST &st, RS *y, int *err) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int4 *trec = T.task_rec + 4 * (long long)F.task_base;
+    const int *lt = T.lev_tasks + F.levtask_base;
+    const int *rel = T.rel + F.rel_base;
+    const int *rows = T.rows + F.rows_base;
+    for (int g = 0; g < 3 * F.nlev; ++g) {
+        const int a = lt[g], e = lt[g + 1];
+        if (a == e) continue;
+        for (int t = a + warp; t < e; t += nw) {
+            const int4 q1 = trec[4 * t + 1];
+            const int type = g % 3;
+            if (type == 0) {
+                task_diag<RG, RS, ST>(st, q1.x, q1.y, q1.z, y + q1.w, err);
+            } else if (type == 1) {
+                task_panel<RG, ST>(st, q1.x, q1.y, q1.z, q1.w);
+            } else {
+                const int4 q2 = trec[4 * t + 2], q3 = trec[4 * t + 3];
+                task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class RG, class RS, class ST>
+__device__ __forceinline__ void factor_numeric(const FacDev &F, const Tables &T, const ST &st, RS *y,
+                                               int *ctr, int *err) {
+    if (F.level_sched) factor_levels<RG, RS, ST>(F, T, st, y, err);
+    else factor_tasks<RG, RS, ST>(F, T, st, y, ctr, err);
+}
+
+// Forward solve L y = b with a factored storage, level by level: diagonal
+// blocks by one warp each, then the rhs updates of the rows below them in
+// 32-row chunks over all warps.  Must be called by every thread of the block.
+template <class RG, class RS, class ST>
+__device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS *y) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
-    const int *lev_units = T.lev_units + F.levunit_base;
-    const int4 *urec = T.unit_rec + 3 * (long long)F.unit_base;
-    const int *rel = T.rel + F.rel_base;
+    const int *lev_chunks = T.lev_chunks + F.levchunk_base;
+    const int4 *crec = T.chunk_rec + 2 * (long long)F.chunk_base;
     const int *rows = T.rows + F.rows_base;
     for (int lev = 0; lev < F.nlev; ++lev) {
         const int a = lev_off[lev], e = lev_off[lev + 1];
-        // (1a) diagonal blocks: one warp per supernode (at most 32 columns)
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
             const int w = T.sn_w[s];
-            diag_block_any<RG, RS>(st.at(T.sn_off[s]), w, w + T.sn_nr[s], y + T.sn_c0[s], do_factor,
-                                   lane, err);
+            diag_block_any<RG, RS>(st.at(T.sn_off[s]), w, w + T.sn_nr[s], y + T.sn_c0[s], false,
+                                   lane, nullptr);
         }
         __syncthreads();
-        // (1b) rows below the diagonal blocks, 32-row chunks spread over all warps
-        if (do_factor) {
-            const int *lev_chunks = T.lev_chunks + F.levchunk_base;
-            const int4 *crec = T.chunk_rec + F.chunk_base;
-            const int k1 = lev_chunks[lev + 1];
-            const int k0 = lev_chunks[lev];
-            if (k1 > k0) {
-                for (int k = k0 + warp; k < k1; k += nw) {
-                    const int4 r = crec[k];
-                    panel_rows_any<RG>(st.at(r.x), r.y, r.z, r.w, lane);
-                }
-                __syncthreads();
-            }
-        }
-        // (2) updates of ancestors and of the trailing Schur block
-        if (do_factor) {
-            // column units: a warp takes one (supernode, target column j) and its
-            // lanes walk rows i >= j; unit j = 0 also carries the rhs update.
-            // Records are packed and the next one is fetched ahead.
-            // pipeline: records two units ahead, first target row one unit ahead.
-            // A unit covers up to four target columns j0 .. j0+nj of one segment:
-            // each row loads its L values and its target row once.
-            const int u1 = lev_units[lev + 1];
-            int u = lev_units[lev] + warp;
-            const int4 z4 = make_int4(0, 0, 0, 0);
-            int4 ra = z4, rb = z4, rc = z4, na = z4, nb = z4, nc = z4;
-            int tg0 = 0;
-            if (u < u1) {
-                ra = urec[3 * u];
-                rb = urec[3 * u + 1];
-                rc = urec[3 * u + 2];
-                const int ir = rb.z + lane;
-                if (ir < rb.y - rb.x) tg0 = rel[ra.y + ir];
-            }
-            if (u + nw < u1) {
-                na = urec[3 * (u + nw)];
-                nb = urec[3 * (u + nw) + 1];
-                nc = urec[3 * (u + nw) + 2];
-            }
-            while (u < u1) {
-                const int un = u + nw, unn = u + 2 * nw;
-                int tgn = 0;
-                if (un < u1) {
-                    const int ir = nb.z + lane;
-                    if (ir < nb.y - nb.x) tgn = rel[na.y + ir];
-                }
-                int4 nna = z4, nnb = z4, nnc = z4;
-                if (unn < u1) {
-                    nna = urec[3 * unn];
-                    nnb = urec[3 * unn + 1];
-                    nnc = urec[3 * unn + 2];
-                }
-                const RG *Ps = st.at(ra.x);
-                const int *relp = rel + ra.y;
-                const int *rws = rows + ra.z;
-                const RS *yc = y + ra.w;
-                const int w = rb.x, ld = rb.y, j0 = rb.z, nj = rb.w;
-                if (j0 == 0) {
-                    switch (nj) {
-                        case 1: unit_rows<RG, RS, 1, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 2: unit_rows<RG, RS, 2, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 3: unit_rows<RG, RS, 3, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        default: unit_rows<RG, RS, 4, true, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                    }
-                } else {
-                    switch (nj) {
-                        case 1: unit_rows<RG, RS, 1, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 2: unit_rows<RG, RS, 2, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        case 3: unit_rows<RG, RS, 3, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                        default: unit_rows<RG, RS, 4, false, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rc, tg0, lane); break;
-                    }
-                }
-                ra = na;
-                rb = nb;
-                rc = nc;
-                tg0 = tgn;
-                na = nna;
-                nb = nnb;
-                nc = nnc;
-                u = un;
-            }
-        } else {
-            for (int i = a + warp; i < e; i += nw) {
-                const int s = F.sn_base + sn_order[i];
-                const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R;
-                const RG *Ps = st.at(T.sn_off[s]) + w;
-                const int rb = F.rows_base + T.sn_rows[s];
-                const RS *yc = y + T.sn_c0[s];
-                for (int ir = lane; ir < R; ir += 32) {
-                    RS v = RS(0);
-                    for (int c = 0; c < w; ++c) v += RS(Ps[(size_t)c * ld + ir]) * yc[c];
-                    atomicAdd(y + T.rows[rb + ir], -v);
-                }
+        for (int k = lev_chunks[lev] + warp; k < lev_chunks[lev + 1]; k += nw) {
+            const int4 r = crec[2 * k], r2 = crec[2 * k + 1];
+            const RG *P = st.at(r.x);
+            const int w = r.y, ld = r.z, row = r.w + lane;
+            if (row < ld) {
+                const RS *yc = y + r2.x;
+                RS v = RS(0);
+                for (int c = 0; c < w; ++c) v += RS(P[(size_t)c * ld + row]) * yc[c];
+                atomicAdd(y + rows[r2.y + row - w], -v);
             }
         }
         __syncthreads();
@@ -427,28 +550,50 @@ __device__ void factor_forward(const FacDev &F, const Tables &T, const ST &st, R
 // y[0..n_int) holds the interior solution (Eq. backsub).
 template <class RG, class RS, class ST>
 __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y) {
+    constexpr unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
+    const int *lev_chunks = T.lev_chunks + F.levchunk_base;
+    const int4 *crec = T.chunk_rec + 2 * (long long)F.chunk_base;
+    const int *rows = T.rows + F.rows_base;
     for (int lev = F.nlev - 1; lev >= 0; --lev) {
+        // (a) contributions of the (already solved) rows below each diagonal block,
+        //     32-row chunks over all warps, reduced per column
+        for (int k = lev_chunks[lev] + warp; k < lev_chunks[lev + 1]; k += nw) {
+            const int4 r = crec[2 * k], r2 = crec[2 * k + 1];
+            const RG *P = st.at(r.x);
+            const int w = r.y, ld = r.z, row = r.w + lane;
+            const RS xi = row < ld ? y[rows[r2.y + row - w]] : RS(0);
+            for (int c = 0; c < w; ++c) {
+                RS v = row < ld ? RS(P[(size_t)c * ld + row]) * xi : RS(0);
+                v = warp_sum(v);
+                if (lane == 0) atomicAdd(y + r2.x + c, -v);
+            }
+        }
+        __syncthreads();
+        // (b) backward substitution with the diagonal block (lane r holds y_r)
         const int a = lev_off[lev], e = lev_off[lev + 1];
         for (int i = a + warp; i < e; i += nw) {
             const int s = F.sn_base + sn_order[i];
-            const int w = T.sn_w[s], R = T.sn_nr[s], ld = w + R, c0 = T.sn_c0[s];
+            const int w = T.sn_w[s], ld = w + T.sn_nr[s], c0 = T.sn_c0[s];
             const RG *P = st.at(T.sn_off[s]);
-            const int *rows = T.rows + F.rows_base + T.sn_rows[s];
-            for (int c = 0; c < w; ++c) {
-                RS acc = RS(0);
-                for (int i2 = lane; i2 < R; i2 += 32) acc += RS(P[(size_t)c * ld + w + i2]) * y[rows[i2]];
-                acc = warp_sum(acc);
-                if (lane == 0) y[c0 + c] -= acc;
-            }
-            __syncwarp();
-            for (int c = w - 1; c >= 0; --c) {
-                RS acc = RS(0);
-                for (int r = c + 1 + lane; r < w; r += 32) acc += RS(P[(size_t)c * ld + r]) * y[c0 + r];
-                acc = warp_sum(acc);
-                if (lane == 0) y[c0 + c] = (y[c0 + c] - acc) * RS(P[(size_t)c * ld + c]);
+            for (int kb = ((w - 1) / 32) * 32; kb >= 0; kb -= 32) {
+                const int r = kb + lane;
+                RS t = r < w ? y[c0 + r] : RS(0);
+                for (int c = min(w, kb + 32) - 1; c >= kb; --c) {
+                    const RS xc = __shfl_sync(FULL, t * RS(P[(size_t)c * ld + c]), c - kb);
+                    if (lane == c - kb) t = xc;
+                    else if (r < c) t -= RS(P[(size_t)r * ld + c]) * xc;
+                }
+                if (r < w) y[c0 + r] = t;
+                __syncwarp();
+                // earlier column blocks of a panel wider than 32 see this block's solution
+                for (int rr = lane; rr < kb; rr += 32) {
+                    RS v = RS(0);
+                    for (int c = kb; c < min(w, kb + 32); ++c) v += RS(P[(size_t)rr * ld + c]) * y[c0 + c];
+                    y[c0 + rr] -= v;
+                }
                 __syncwarp();
             }
         }
@@ -662,7 +807,8 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     for (int i = tid; i < nv; i += nt) y[i] = RS(g[i]);
     __syncthreads();
     // ---- Schur-mode factorisation (Sec. 4.3): leaves S_b and b_hat in the trailing block
-    factor_forward<RG, RS>(A.F, T, FlatStore<RG>{st}, y, true, &s_err);
+    // the bus-value region is free from here on: task counters
+    factor_tasks<RG, RS>(A.F, T, FlatStore<RG>{st}, y, (int *)(smem + A.off_bus), &s_err);
     // ---- outputs
     if (A.in_smem) {
         RG *dst = fac + A.fac_base + (long long)s * A.fac_stride;
@@ -675,7 +821,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     const double Js = block_sum(Jloc, red);
     if (tid == 0) {
         atomicAdd(X.J + s, Js);
-        if (s_err) atomicOr(X.err + s, 1);
+        if (s_err) atomicOr(X.err + s, s_err);
     }
 }
 
@@ -688,9 +834,12 @@ struct BndDev {
     const int *asm_beg, *asm_area, *asm_off;
     const int *rhs_beg, *rhs_area, *rhs_lv;
     const int *bvar_ibus, *bvar_isT;
+    const long long *asm_abs, *rhs_abs;   // absolute gather sources for snapshot 0
+    const int *asm_str, *rhs_str;         // their per-snapshot strides
     long long stride;     // storage elements per snapshot
     int split;            // storage entries from here on live in shared memory
-    int smem_off_st;      // their byte offset in dynamic shared memory
+    int smem_off_ctr;     // byte offset of the task counters (2 nsn + 1 ints)
+    int smem_off_st;      // byte offset of the shared part of the storage
 };
 
 template <class RG, class RS>
@@ -714,24 +863,20 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
     if (tid == 0) s_err = 0;
     for (int P = tid; P < B.F.store_total; P += nt) {
         RG v = RG(0);
-        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i) {
-            const AreaDev &A = areas[B.asm_area[i]];
-            v += fac[A.fac_base + (long long)s * A.fac_stride + B.asm_off[i]];
-        }
+        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i)
+            v += fac[B.asm_abs[i] + (long long)s * B.asm_str[i]];
         *st.at(P) = v;
         Am[P] = v;
     }
     for (int gi = tid; gi < nG; gi += nt) {
         double v = 0.0;
-        for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i) {
-            const AreaDev &A = areas[B.rhs_area[i]];
-            v += bh[A.bh_base + (long long)s * A.F.n_bnd + B.rhs_lv[i]];
-        }
+        for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i)
+            v += bh[B.rhs_abs[i] + (long long)s * B.rhs_str[i]];
         bhat[gi] = v;
         y[gi] = RS(v);
     }
     __syncthreads();
-    factor_forward<RG, RS>(B.F, T, st, y, true, &s_err);
+    factor_numeric<RG, RS>(B.F, T, st, y, (int *)(smem + B.smem_off_ctr), &s_err);
     back_solve<RG, RS>(B.F, T, st, y);
     for (int gi = tid; gi < nG; gi += nt) x[gi] = double(y[gi]);
     __syncthreads();
@@ -765,7 +910,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
         __syncthreads();
         for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
         __syncthreads();
-        factor_forward<RG, RS>(B.F, T, st, y, false, &s_err);
+        solve_forward<RG, RS>(B.F, T, st, y);
         back_solve<RG, RS>(B.F, T, st, y);
         for (int gi = tid; gi < nG; gi += nt) x[gi] += double(y[gi]);
         __syncthreads();
@@ -785,7 +930,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
     mx = block_max(mx, red);
     if (tid == 0) {
         atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
-        if (s_err) atomicOr(X.err + s, 1);
+        if (s_err) atomicOr(X.err + s, s_err);
     }
 }
 

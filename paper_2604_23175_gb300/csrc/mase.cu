@@ -71,14 +71,13 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
     app(H.relbase, F.relbase);
     d.rel_base = (int)H.rel.size();
     app(H.rel, F.rel);
-    d.unit_base = (int)H.unit_sn.size();
-    app(H.unit_sn, F.unit_sn);
-    app(H.unit_j, F.unit_j);
-    d.levunit_base = (int)H.lev_units.size();
-    if (F.lev_units.empty()) H.lev_units.push_back(0);
-    else app(H.lev_units, F.lev_units);
-    app(H.unit_rec, F.unit_rec);
-    d.chunk_base = (int)H.chunk_rec.size() / 4;
+    d.task_base = (int)(H.tasks.size() / 16);
+    d.n_tasks = F.n_tasks;
+    app(H.tasks, F.tasks);
+    d.level_sched = F.level_sched;
+    d.levtask_base = (int)H.lev_tasks.size();
+    app(H.lev_tasks, F.lev_tasks);
+    d.chunk_base = (int)H.chunk_rec.size() / 8;
     app(H.chunk_rec, F.chunk_rec);
     d.levchunk_base = (int)H.lev_chunks.size();
     if (F.lev_chunks.empty()) H.lev_chunks.push_back(0);
@@ -295,6 +294,9 @@ int build(mase_handle *h) {
         }
         if (o > (size_t)h->smem_limit)
             return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large for shared memory");
+        // the factorisation's task counters reuse the bus-value region
+        if ((2 * (size_t)A.F.nsn() + 1) * sizeof(int) > 3 * (size_t)A.nb_loc * sizeof(double))
+            return set_err(MASE_EINVAL, "area " + std::to_string(k) + ": task counters do not fit");
         max_local = std::max(max_local, (size_t)d.smem_bytes);
         d.back_smem_bytes = (int)(((size_t)nv * sizeof(RS) + 15) & ~size_t(15));
         max_back = std::max(max_back, (size_t)d.back_smem_bytes);
@@ -330,7 +332,10 @@ int build(mase_handle *h) {
     bd.stride = B.F.store_total;
     {
         // vectors first, then as much of the top of the boundary factor as fits
-        const size_t vec = (((size_t)B.n_gamma * (3 * sizeof(double) + sizeof(RS))) + 15) & ~size_t(15);
+        const size_t vec0 = (((size_t)B.n_gamma * (3 * sizeof(double) + sizeof(RS))) + 15) & ~size_t(15);
+        // task counters of the dataflow factorisation
+        const size_t vec = vec0 + ((((size_t)2 * B.F.nsn() + 1) * sizeof(int) + 15) & ~size_t(15));
+        bd.smem_off_ctr = (int)vec0;
         if (vec > (size_t)h->smem_limit)
             return set_err(MASE_EINVAL, "boundary system too large for shared-memory vectors");
         const long long room = ((long long)h->smem_limit - (long long)vec) / (long long)sizeof(RG);
@@ -373,6 +378,29 @@ int build(mase_handle *h) {
     CK(h->b_rhs_lv.upload(B.rhs_lv, st));
     CK(h->b_bvar_ibus.upload(B.bvar_ibus, st));
     CK(h->b_bvar_isT.upload(B.bvar_isT, st));
+    {
+        // absolute gather sources: instance base + offset, plus the per-snapshot stride
+        std::vector<long long> aabs(B.asm_area.size()), rabs(B.rhs_area.size());
+        std::vector<int> astr(B.asm_area.size()), rstr(B.rhs_area.size());
+        for (size_t i = 0; i < B.asm_area.size(); ++i) {
+            const AreaDev &A = h->areas_h[B.asm_area[i]];
+            aabs[i] = A.fac_base + B.asm_off[i];
+            astr[i] = A.fac_stride;
+        }
+        for (size_t i = 0; i < B.rhs_area.size(); ++i) {
+            const AreaDev &A = h->areas_h[B.rhs_area[i]];
+            rabs[i] = A.bh_base + B.rhs_lv[i];
+            rstr[i] = A.F.n_bnd;
+        }
+        CK(h->b_asm_abs.upload(aabs, st));
+        CK(h->b_asm_str.upload(astr, st));
+        CK(h->b_rhs_abs.upload(rabs, st));
+        CK(h->b_rhs_str.upload(rstr, st));
+        bd.asm_abs = h->b_asm_abs.p;
+        bd.asm_str = h->b_asm_str.p;
+        bd.rhs_abs = h->b_rhs_abs.p;
+        bd.rhs_str = h->b_rhs_str.p;
+    }
     bd.asm_beg = h->b_asm_beg.p;
     bd.asm_area = h->b_asm_area.p;
     bd.asm_off = h->b_asm_off.p;
@@ -397,17 +425,13 @@ int build(mase_handle *h) {
     T.slot_q = h->t_slot_q.p; T.slot_ebeg = h->t_slot_ebeg.p; T.slot_ecnt = h->t_slot_ecnt.p;
     T.item_own = h->t_item_own.p; T.item_uv = h->t_item_uv.p; T.item_pos = h->t_item_pos.p;
     T.ebnd = h->t_ebnd.p;
-    CK(h->t_unit_sn.upload(H.unit_sn, st));
-    CK(h->t_unit_j.upload(H.unit_j, st));
-    CK(h->t_lev_units.upload(H.lev_units, st));
-    T.unit_sn = h->t_unit_sn.p;
-    T.unit_j = h->t_unit_j.p;
-    T.lev_units = h->t_lev_units.p;
-    CK(h->t_unit_rec.upload(H.unit_rec, st));
+    CK(h->t_tasks.upload(H.tasks.empty() ? std::vector<int>(16, 0) : H.tasks, st));
+    T.task_rec = reinterpret_cast<const int4 *>(h->t_tasks.p);
+    CK(h->t_lev_tasks.upload(H.lev_tasks, st));
+    T.lev_tasks = h->t_lev_tasks.p;
     CK(h->t_item_rec.upload(H.item_rec, st));
-    T.unit_rec = reinterpret_cast<const int4 *>(h->t_unit_rec.p);
     T.item_rec = reinterpret_cast<const int4 *>(h->t_item_rec.p);
-    CK(h->t_chunk_rec.upload(H.chunk_rec.empty() ? std::vector<int>(4, 0) : H.chunk_rec, st));
+    CK(h->t_chunk_rec.upload(H.chunk_rec.empty() ? std::vector<int>(8, 0) : H.chunk_rec, st));
     CK(h->t_lev_chunks.upload(H.lev_chunks, st));
     T.chunk_rec = reinterpret_cast<const int4 *>(h->t_chunk_rec.p);
     T.lev_chunks = h->t_lev_chunks.p;

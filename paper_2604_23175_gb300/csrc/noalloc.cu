@@ -50,7 +50,7 @@ struct Tabs {
     const int *off_B;            // per area: Schur-block offset in the instance storage
     const int *n_bnd;            // per area: local boundary unknowns
     const int *xg_of_b;          // boundary-system unknown -> x_Gamma index
-    int *status;                 // per snapshot: 1 = non-SPD pivot, 2 = non-finite
+    int *status;                 // per snapshot: 1 = non-SPD pivot, 2 = non-finite, 4 = a bounded wait gave up
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
         y[gi] = RS(v);
     }
     __syncthreads();
-    factor_forward<RG, RS>(B.F, T, FlatStore<RG>{st}, y, true, &s_err);
+    factor_numeric<RG, RS>(B.F, T, FlatStore<RG>{st}, y, (int *)(smem + B.smem_off_ctr), &s_err);
     back_solve<RG, RS>(B.F, T, FlatStore<RG>{st}, y);
     for (int gi = tid; gi < nG; gi += nt) x[gi] = double(y[gi]);
     __syncthreads();
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
         __syncthreads();
         for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
         __syncthreads();
-        factor_forward<RG, RS>(B.F, T, FlatStore<RG>{st}, y, false, &s_err);
+        solve_forward<RG, RS>(B.F, T, FlatStore<RG>{st}, y);
         back_solve<RG, RS>(B.F, T, FlatStore<RG>{st}, y);
         for (int gi = tid; gi < nG; gi += nt) x[gi] += double(y[gi]);
         __syncthreads();
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
     }
     if (bad) atomicOr(tb.status + s, 2);
     __syncthreads();
-    if (tid == 0 && s_err) atomicOr(tb.status + s, 1);
+    if (tid == 0 && s_err) atomicOr(tb.status + s, s_err);
 }
 
 bool is_device(const void *p) {
@@ -259,6 +259,7 @@ int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const doubl
         (e = cudaStreamWaitEvent(v.user_stream, v.ev_out, 0)) != cudaSuccess)
         return fail(MASE_EDEVICE, std::string("coordinator: ") + cudaGetErrorString(e));
     for (int s = 0; s < S; ++s) {
+        if (status[s] & 4) return fail(MASE_EDEVICE, "a bounded device-side wait gave up");
         if (status[s] & 1) return fail(MASE_EUNOBSERVABLE, "non-positive pivot in the boundary system");
         if (status[s] & 2) return fail(MASE_ENONFINITE, "non-finite boundary step");
     }

@@ -2,6 +2,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <queue>
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
@@ -60,7 +61,199 @@ int SymFactor::pos(int r, int c) const {
     return sn_off[t] + (c - c0) * ld + rp;
 }
 
-SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wmax) {
+// Dataflow task list of the numeric factorisation (Sec. 4.3 Schur mode).
+// Tasks: D(s) factors the diagonal block of supernode s and forward-solves its
+// rhs; C(s, r0) solves 32 rows of the panel below it; U(s, j0) applies up to
+// kUnitCols target columns of s's update to an ancestor (or to the trailing
+// Schur block) and, when j0 starts a target segment, that segment's rhs rows.
+// Counters: ctr[t] counts finished updates into supernode t, ctr[nsn + s]
+// counts finished D(s) and C(s, .) tasks.  The order is a list schedule of
+// nwarps workers with estimated cycle costs, highest bottom level first among
+// the ready tasks, so it is a topological order in which warps that take the
+// next task rarely wait.
+void build_tasks(SymFactor &F, int nwarps, bool level_sched) {
+    const int nsn = F.nsn();
+    F.tasks.clear();
+    F.n_tasks = 0;
+    F.level_sched = level_sched ? 1 : 0;
+    F.lev_tasks.assign(3 * (size_t)F.nlev() + 1, 0);
+    if (nsn == 0) return;
+    struct Task {
+        int type, s, idx;   // idx: r0 (chunk) or unit number
+        double cost;
+    };
+    std::vector<Task> tk;
+    std::vector<int> d_of(nsn), nchunk(nsn, 0), nin(nsn, 0);
+    std::vector<std::vector<int>> c_of(nsn), u_of(nsn), u_into(nsn);
+    for (int s = 0; s < nsn; ++s) {
+        const int w = F.sn_w[s], ld = w + F.sn_nr[s];
+        d_of[s] = (int)tk.size();
+        tk.push_back({0, s, 0, 400.0 + 350.0 * w});
+        for (int r0 = w; r0 < ld; r0 += 32) {
+            c_of[s].push_back((int)tk.size());
+            tk.push_back({1, s, r0, 300.0 + 200.0 * w});
+            ++nchunk[s];
+        }
+    }
+    std::vector<int> u_tgt(F.unit_sn.size()), u_rhs(F.unit_sn.size(), 0);
+    for (size_t u = 0; u < F.unit_sn.size(); ++u) {
+        const int s = F.unit_sn[u], j = F.unit_j[u], nj = F.unit_nj[u], w = F.sn_w[s];
+        const int R = F.sn_nr[s], rb = F.sn_rows[s];
+        auto tgt = [&](int jj) {
+            const int c = F.rows[rb + jj];
+            return c < F.n_int ? F.var_sn[c] : -1;
+        };
+        const int t = tgt(j);
+        u_tgt[u] = t;
+        if (j == 0 || tgt(j - 1) != t) {
+            int e = j + 1;
+            while (e < R && tgt(e) == t) ++e;
+            u_rhs[u] = e;
+        }
+        const int tid = (int)tk.size();
+        const double iters = std::ceil((R - j) / 32.0);
+        tk.push_back({2, s, (int)u, 300.0 + iters * (w * (20.0 + 5.0 * nj) + 150.0)});
+        u_of[s].push_back(tid);
+        if (t >= 0) {
+            u_into[t].push_back(tid);
+            ++nin[t];
+        }
+    }
+    const int nt = (int)tk.size();
+    // successors and predecessor counts
+    std::vector<std::vector<int>> succ(nt);
+    std::vector<int> npred(nt, 0);
+    auto edge = [&](int a, int b) {
+        succ[a].push_back(b);
+        ++npred[b];
+    };
+    for (int s = 0; s < nsn; ++s) {
+        for (int c : c_of[s]) edge(d_of[s], c);
+        for (int u : u_of[s]) {
+            edge(d_of[s], u);
+            for (int c : c_of[s]) edge(c, u);
+        }
+        for (int u : u_into[s]) edge(u, d_of[s]);
+    }
+    // bottom levels (longest cost path to a sink); tasks were created with
+    // every edge pointing to a later D, or from D/C to U of the same s
+    std::vector<double> bl(nt, 0.0);
+    {
+        // reverse topological order by Kahn on the reversed graph
+        std::vector<int> nsucc(nt), order;
+        order.reserve(nt);
+        for (int i = 0; i < nt; ++i) {
+            nsucc[i] = (int)succ[i].size();
+            if (!nsucc[i]) order.push_back(i);
+        }
+        std::vector<std::vector<int>> pred(nt);
+        for (int i = 0; i < nt; ++i)
+            for (int j : succ[i]) pred[j].push_back(i);
+        for (size_t q = 0; q < order.size(); ++q) {
+            const int i = order[q];
+            double m = 0.0;
+            for (int j : succ[i]) m = std::max(m, bl[j]);
+            bl[i] = tk[i].cost + m;
+            for (int p : pred[i])
+                if (--nsucc[p] == 0) order.push_back(p);
+        }
+        if ((int)order.size() != nt) fail("symbolic: task graph has a cycle");
+    }
+    // list schedule: the earliest free warp takes the ready task of highest
+    // bottom level, else the task that becomes ready first
+    std::vector<double> ready(nt, 0.0), fin(nt, 0.0);
+    std::vector<int> left = npred;
+    using PQ = std::pair<double, int>;
+    std::priority_queue<PQ, std::vector<PQ>, std::greater<PQ>> pending;   // by ready time
+    std::priority_queue<PQ> avail;                                         // by bottom level
+    for (int i = 0; i < nt; ++i)
+        if (!left[i]) pending.push({0.0, i});
+    std::priority_queue<double, std::vector<double>, std::greater<double>> wfree;
+    for (int w = 0; w < std::max(1, nwarps); ++w) wfree.push(0.0);
+    std::vector<int> order;
+    order.reserve(nt);
+    while ((int)order.size() < nt) {
+        const double tau = wfree.top();
+        wfree.pop();
+        while (!pending.empty() && pending.top().first <= tau) {
+            avail.push({bl[pending.top().second], pending.top().second});
+            pending.pop();
+        }
+        int i;
+        if (!avail.empty()) {
+            i = avail.top().second;
+            avail.pop();
+        } else {
+            if (pending.empty()) fail("symbolic: task schedule stalled");
+            i = pending.top().second;
+            pending.pop();
+        }
+        const double start = std::max(tau, ready[i]);
+        fin[i] = start + tk[i].cost;
+        wfree.push(fin[i]);
+        order.push_back(i);
+        for (int j : succ[i]) {
+            ready[j] = std::max(ready[j], fin[i]);
+            if (--left[j] == 0) pending.push({ready[j], j});
+        }
+    }
+    if (level_sched) {
+        std::vector<int> lev(nsn, 0);
+        for (int l = 0; l < F.nlev(); ++l)
+            for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) lev[F.sn_order[i]] = l;
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (lev[tk[a].s] != lev[tk[b].s]) return lev[tk[a].s] < lev[tk[b].s];
+            return tk[a].type < tk[b].type;
+        });
+        int q = 0;
+        for (int l = 0; l < F.nlev(); ++l)
+            for (int ty = 0; ty < 3; ++ty) {
+                F.lev_tasks[3 * l + ty] = q;
+                while (q < nt && lev[tk[order[q]].s] == l && tk[order[q]].type == ty) ++q;
+            }
+        F.lev_tasks[3 * F.nlev()] = q;
+        if (q != nt) fail("symbolic: level task groups incomplete");
+    }
+    // records
+    F.tasks.assign((size_t)nt * 16, 0);
+    for (int q = 0; q < nt; ++q) {
+        const Task &T = tk[order[q]];
+        int *r = F.tasks.data() + (size_t)q * 16;
+        const int s = T.s, w = F.sn_w[s], ld = w + F.sn_nr[s];
+        if (T.type == 0) {
+            r[0] = (0 << 24) | s;
+            r[1] = s;
+            r[2] = nin[s];
+            r[3] = nsn + s;
+            r[4] = F.sn_off[s]; r[5] = w; r[6] = ld; r[7] = F.sn_c0[s];
+        } else if (T.type == 1) {
+            r[0] = (1 << 24) | s;
+            r[1] = nsn + s;
+            r[2] = 1;
+            r[3] = nsn + s;
+            r[4] = F.sn_off[s]; r[5] = w; r[6] = ld; r[7] = T.idx;
+        } else {
+            const int u = T.idx, j = F.unit_j[u], nj = F.unit_nj[u], rb = F.sn_rows[s];
+            r[0] = (2 << 24) | s;
+            r[1] = nsn + s;
+            r[2] = 1 + nchunk[s];
+            r[3] = u_tgt[u] >= 0 ? u_tgt[u] : -1;
+            r[4] = F.sn_off[s] + w; r[5] = F.relbase[rb + j]; r[6] = rb; r[7] = F.sn_c0[s];
+            r[8] = w | (nj << 8); r[9] = ld | (j << 16); r[10] = u_rhs[u];
+            for (int k = 0; k < nj; ++k) r[11 + k] = F.colbase[rb + j + k];
+        }
+    }
+    F.n_tasks = nt;
+    // estimated makespan of the schedule (cycles)
+    double mk = 0.0;
+    for (int i = 0; i < nt; ++i) mk = std::max(mk, fin[i]);
+    F.sched_cycles = mk;
+}
+
+SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wmax, int max_panel,
+                         bool level_sched) {
+    if (max_panel < 1 || max_panel > kMaxPanel) fail("symbolic: panel width out of range");
     const int ni = sys.nb_int, nbn = sys.nb_bnd, n = ni + nbn;
     SymResult out;
     // --- exact minimum degree on the elimination graph (dense bitmap) ---
@@ -240,7 +433,7 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
             if (starts[p]) sn_first.push_back(p);
         (void)group_start;
     }
-    // Supernodes wider than kMaxPanel scalars are cut into consecutive pieces:
+    // Supernodes wider than max_panel scalars are cut into consecutive pieces:
     // a piece's structure is the later columns of the supernode plus its rows,
     // so each piece is a valid supernode and the pieces form a chain.
     {
@@ -252,7 +445,7 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
             while (p < p1) {
                 cut.push_back(p);
                 int wsc = 0, q = p;
-                while (q < p1 && wsc + sys.nvar[out.order[q]] <= kMaxPanel) wsc += sys.nvar[out.order[q++]];
+                while (q < p1 && wsc + sys.nvar[out.order[q]] <= max_panel) wsc += sys.nvar[out.order[q++]];
                 if (q == p) ++q;
                 p = q;
             }
@@ -372,11 +565,11 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
         for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
             const int s = F.sn_order[i], w = F.sn_w[s], ld = w + F.sn_nr[s];
             for (int r0 = w; r0 < ld; r0 += 32) {
-                const int rec[4] = {F.sn_off[s], w, ld, r0};
-                F.chunk_rec.insert(F.chunk_rec.end(), rec, rec + 4);
+                const int rec[8] = {F.sn_off[s], w, ld, r0, F.sn_c0[s], F.sn_rows[s], 0, 0};
+                F.chunk_rec.insert(F.chunk_rec.end(), rec, rec + 8);
             }
         }
-        F.lev_chunks[l + 1] = (int)F.chunk_rec.size() / 4;
+        F.lev_chunks[l + 1] = (int)F.chunk_rec.size() / 8;
     }
     // update units: consecutive target columns of one segment, kUnitCols at most
     F.lev_units.assign(nlev + 1, 0);
@@ -394,14 +587,7 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
         }
         F.lev_units[l + 1] = (int)F.unit_sn.size();
     }
-    F.unit_rec.reserve(12 * F.unit_sn.size());
-    for (size_t u = 0; u < F.unit_sn.size(); ++u) {
-        const int s = F.unit_sn[u], j = F.unit_j[u], nj = F.unit_nj[u], w = F.sn_w[s], R = F.sn_nr[s];
-        const int rb = F.sn_rows[s];
-        int rec[12] = {F.sn_off[s] + w, F.relbase[rb + j], rb, F.sn_c0[s], w, w + R, j, nj, 0, 0, 0, 0};
-        for (int k = 0; k < nj; ++k) rec[8 + k] = F.colbase[rb + j + k];
-        F.unit_rec.insert(F.unit_rec.end(), rec, rec + 12);
-    }
+    build_tasks(F, kTaskWarps, level_sched);
     return out;
 }
 
@@ -546,7 +732,7 @@ bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st,
                 std::sort(v.begin(), v.end());
                 v.erase(std::unique(v.begin(), v.end()), v.end());
             }
-            bsym = build_symbolic(bs);
+            bsym = build_symbolic(bs, 0.30, 16, kBoundaryPanel, true);
             B.F = bsym.F;
         }
         B.n_gamma = B.F.n_int;
@@ -787,60 +973,123 @@ struct Rng {
     double sym() { return 2.0 * next() - 1.0; }
 };
 
-// serial emulation of the device schedule (panel + scattered updates)
-void host_factor(const SymFactor &F, std::vector<double> &st, std::vector<double> &y, bool factor) {
+// one task of the dataflow factorisation, as the device runs it
+void host_task(const SymFactor &F, const int *r, std::vector<double> &st, std::vector<double> &y) {
+    const int type = r[0] >> 24;
+    if (type == 0) {
+        const int w = r[5], ld = r[6];
+        double *P = st.data() + r[4];
+        double *yc = y.data() + r[7];
+        for (int c = 0; c < w; ++c) {
+            double *col = P + (size_t)c * ld;
+            double d = col[c];
+            if (!(d > 0)) throw std::runtime_error("selfcheck: non-positive pivot");
+            d = std::sqrt(d);
+            for (int r2 = c + 1; r2 < w; ++r2) col[r2] /= d;
+            col[c] = 1.0 / d;   // diagonal kept as its reciprocal, as on the device
+            for (int c2 = c + 1; c2 < w; ++c2)
+                for (int r2 = c2; r2 < w; ++r2) P[(size_t)c2 * ld + r2] -= col[r2] * col[c2];
+        }
+        for (int c = 0; c < w; ++c) {
+            yc[c] *= P[(size_t)c * ld + c];
+            for (int r2 = c + 1; r2 < w; ++r2) yc[r2] -= P[(size_t)c * ld + r2] * yc[c];
+        }
+    } else if (type == 1) {
+        const int w = r[5], ld = r[6], r0 = r[7];
+        double *P = st.data() + r[4];
+        for (int row = r0; row < std::min(ld, r0 + 32); ++row)
+            for (int c = 0; c < w; ++c) {
+                double v = P[(size_t)c * ld + row];
+                for (int k = 0; k < c; ++k) v -= P[(size_t)k * ld + row] * P[(size_t)k * ld + c];
+                P[(size_t)c * ld + row] = v * P[(size_t)c * ld + c];
+            }
+    } else {
+        const double *Ps = st.data() + r[4];
+        const int *relp = F.rel.data() + r[5];
+        const int rb = r[6], c0 = r[7], w = r[8] & 0xff, nj = r[8] >> 8, ld = r[9] & 0xffff,
+                  j0 = r[9] >> 16, rhs_end = r[10];
+        const int R = ld - w;
+        for (int ir = j0; ir < R; ++ir) {
+            for (int k = 0; k < nj; ++k) {
+                const int jr = j0 + k;
+                if (ir < jr) continue;
+                double v = 0;
+                for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
+                st[r[11 + k] + relp[ir]] -= v;
+            }
+            if (ir < rhs_end) {
+                double vr = 0;
+                for (int c = 0; c < w; ++c) vr += Ps[(size_t)c * ld + ir] * y[c0 + c];
+                y[F.rows[rb + ir]] -= vr;
+            }
+        }
+    }
+}
+
+// Emulation of the device schedules.  Factorisation: warps take tasks in list
+// order and run one whose wait condition holds; the emulation keeps a window
+// of kTaskWarps taken tasks and completes a pseudo-random ready one at a time,
+// so a missing dependency shows up as a wrong result or as a stall.
+void host_factor(const SymFactor &F, std::vector<double> &st, std::vector<double> &y, bool factor,
+                 unsigned long long seed = 1) {
+    if (factor && F.level_sched) {
+        // each group (level, task kind) in a pseudo-random order
+        unsigned long long rs = seed;
+        for (size_t g = 0; g + 1 < F.lev_tasks.size(); ++g) {
+            std::vector<int> grp;
+            for (int t = F.lev_tasks[g]; t < F.lev_tasks[g + 1]; ++t) grp.push_back(t);
+            for (size_t i = grp.size(); i > 1; --i) {
+                rs = rs * 6364136223846793005ull + 1442695040888963407ull;
+                std::swap(grp[i - 1], grp[(rs >> 33) % i]);
+            }
+            for (int t : grp) host_task(F, F.tasks.data() + (size_t)t * 16, st, y);
+        }
+        return;
+    }
+    if (factor) {
+        const int nsn = F.nsn();
+        std::vector<int> ctr(2 * (size_t)nsn, 0);
+        std::vector<int> window;
+        int next = 0;
+        unsigned long long rs = seed;
+        auto rnd = [&rs]() {
+            rs = rs * 6364136223846793005ull + 1442695040888963407ull;
+            return (unsigned)(rs >> 33);
+        };
+        while (next < F.n_tasks || !window.empty()) {
+            while ((int)window.size() < kTaskWarps && next < F.n_tasks) window.push_back(next++);
+            std::vector<int> ok;
+            for (size_t i = 0; i < window.size(); ++i) {
+                const int *r = F.tasks.data() + (size_t)window[i] * 16;
+                if (ctr[r[1]] >= r[2]) ok.push_back((int)i);
+            }
+            if (ok.empty()) throw std::runtime_error("selfcheck: task schedule deadlocks");
+            const int pick = ok[rnd() % ok.size()];
+            const int *r = F.tasks.data() + (size_t)window[pick] * 16;
+            host_task(F, r, st, y);
+            if (r[3] >= 0) ++ctr[r[3]];
+            window.erase(window.begin() + pick);
+        }
+        return;
+    }
     for (int lev = 0; lev < F.nlev(); ++lev) {
         for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
             const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
-            double *P = st.data() + F.sn_off[s];
+            const double *P = st.data() + F.sn_off[s];
             double *yc = y.data() + F.sn_c0[s];
             for (int c = 0; c < w; ++c) {
-                double *col = P + (size_t)c * ld;
-                if (factor) {
-                    double d = col[c];
-                    if (!(d > 0)) throw std::runtime_error("selfcheck: non-positive pivot");
-                    d = std::sqrt(d);
-                    for (int r = c + 1; r < ld; ++r) col[r] /= d;
-                    col[c] = 1.0 / d;   // diagonal kept as its reciprocal, as on the device
-                    for (int c2 = c + 1; c2 < w; ++c2)
-                        for (int r = c2; r < ld; ++r) P[(size_t)c2 * ld + r] -= col[r] * col[c2];
-                }
-                yc[c] *= col[c];
-                for (int r = c + 1; r < w; ++r) yc[r] -= col[r] * yc[c];
+                yc[c] *= P[(size_t)c * ld + c];
+                for (int r = c + 1; r < w; ++r) yc[r] -= P[(size_t)c * ld + r] * yc[c];
             }
         }
-        if (factor) {
-            for (int u = F.lev_units[lev]; u < F.lev_units[lev + 1]; ++u) {
-                const int *rec = F.unit_rec.data() + 12 * (size_t)u;
-                const double *Ps = st.data() + rec[0];
-                const int *relp = F.rel.data() + rec[1];
-                const int rb = rec[2], c0 = rec[3], w = rec[4], ld = rec[5], j0 = rec[6], nj = rec[7];
-                const int R = ld - w;
-                for (int ir = j0; ir < R; ++ir) {
-                    for (int k = 0; k < nj; ++k) {
-                        const int jr = j0 + k;
-                        if (ir < jr) continue;
-                        double v = 0;
-                        for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * Ps[(size_t)c * ld + jr];
-                        st[rec[8 + k] + relp[ir]] -= v;
-                    }
-                    if (j0 == 0) {
-                        double vr = 0;
-                        for (int c = 0; c < w; ++c) vr += Ps[(size_t)c * ld + ir] * y[c0 + c];
-                        y[F.rows[rb + ir]] -= vr;
-                    }
-                }
-            }
-        } else {
-            for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
-                const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
-                const double *Ps = st.data() + F.sn_off[s] + w;
-                const int rb = F.sn_rows[s];
-                for (int ir = 0; ir < R; ++ir) {
-                    double v = 0;
-                    for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
-                    y[F.rows[rb + ir]] -= v;
-                }
+        for (int i = F.lev_off[lev]; i < F.lev_off[lev + 1]; ++i) {
+            const int s = F.sn_order[i], w = F.sn_w[s], R = F.sn_nr[s], ld = w + R;
+            const double *Ps = st.data() + F.sn_off[s] + w;
+            const int rb = F.sn_rows[s];
+            for (int ir = 0; ir < R; ++ir) {
+                double v = 0;
+                for (int c = 0; c < w; ++c) v += Ps[(size_t)c * ld + ir] * y[F.sn_c0[s] + c];
+                y[F.rows[rb + ir]] -= v;
             }
         }
     }

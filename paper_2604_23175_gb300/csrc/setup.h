@@ -40,11 +40,26 @@ struct SymFactor {
     // unit_sn[u]'s row set, all in one target segment (they share the
     // relative-index array); units of level l are [lev_units[l], lev_units[l+1])
     std::vector<int> unit_sn, unit_j, unit_nj, lev_units;
-    // packed unit records, 12 ints each: {sn_off + w, relbase, sn_rows, c0},
-    // {w, ld, j0, nj}, {colbase of the (up to 4) target columns}
-    std::vector<int> unit_rec;
+    // dataflow task records of the numeric factorisation, 16 ints each:
+    // {type << 24 | s, wait counter, wait threshold, counter to signal or -1},
+    // then per type
+    //   D (0): {sn_off, w, ld, c0}
+    //   C (1): {sn_off, w, ld, r0}
+    //   U (2): {sn_off + w, relbase, sn_rows, c0}, {w | nj << 8, ld | j0 << 16,
+    //          rhs end (0: no rhs rows), colbase 0}, {colbase 1..3, 0}
+    // counters: [0, nsn) updates received by supernode t, [nsn, 2 nsn)
+    // diagonal block and panel chunks finished for supernode s
+    std::vector<int> tasks;
+    int n_tasks = 0;
+    // level schedule instead of dataflow: level l runs tasks
+    // [lev_tasks[3l], lev_tasks[3l+1]) (D), then [.., lev_tasks[3l+2]) (C),
+    // then [.., lev_tasks[3l+3]) (U), with a block barrier after each group
+    int level_sched = 0;
+    std::vector<int> lev_tasks;
+    double sched_cycles = 0.0;           // estimated makespan of the task order
     // row chunks of the panels below their diagonal blocks: level l owns
-    // records [lev_chunks[l], lev_chunks[l+1]), 4 ints each {sn_off, w, ld, r0}
+    // records [lev_chunks[l], lev_chunks[l+1]), 8 ints each
+    // {sn_off, w, ld, r0, c0, sn_rows, 0, 0}
     std::vector<int> chunk_rec, lev_chunks;
 
     std::vector<int> var_sn;             // internal scalar var -> supernode
@@ -60,10 +75,21 @@ struct SymFactor {
 };
 
 // Widest supernode panel, in scalar columns: one warp factors a diagonal block
-// of at most this width in registers.
+// of at most this width (wider than 16 as 2 x 2 blocks of 16).  Area factors
+// run as a dataflow whose critical path grows with the panel width, so they
+// use narrower panels than the level-scheduled boundary factor.
 constexpr int kMaxPanel = 32;
+constexpr int kAreaPanel = 16;
+constexpr int kBoundaryPanel = 32;
 // Target columns handled together by one update unit.
 constexpr int kUnitCols = 4;
+// Warps the task order is scheduled for (512-thread blocks).
+constexpr int kTaskWarps = 16;
+
+// builds F.tasks (needs the units, chunks and update maps of F): a list
+// schedule for the dataflow, or (level_sched) level by level with the
+// diagonal blocks, panel chunks and units of each level in F.lev_tasks
+void build_tasks(SymFactor &F, int nwarps, bool level_sched);
 
 // Bus-level system: nodes [0, nb_int) are eliminated in a fill-reducing
 // order, nodes [nb_int, nb_int + nb_bnd) are kept (in the given order).
@@ -85,7 +111,8 @@ struct SymResult {
 // relax_alpha bounds the explicit zeros a merge may add (fraction of the
 // merged panel), relax_wmax the merged width in buses; 0 gives fundamental
 // supernodes only.
-SymResult build_symbolic(const BusSystem &sys, double relax_alpha = 0.30, int relax_wmax = 16);
+SymResult build_symbolic(const BusSystem &sys, double relax_alpha = 0.30, int relax_wmax = 16,
+                         int max_panel = kAreaPanel, bool level_sched = false);
 
 // Dynamic shared-memory layout of the area kernel for one area (byte
 // offsets, 16-byte aligned): FP64 gradient, rhs in the solve type, bus
