@@ -65,8 +65,9 @@ extern "C" {
 
 /* precision modes */
 #define MASE_FP64   0   /* every step in FP64 (the plain comparator)               */
-#define MASE_MIXED  1   /* FP32 gain, factor, Schur and local solves; FP64 residual,
-                           gradient H^T W r, boundary refinement and update        */
+#define MASE_MIXED  1   /* FP32 gain, factor, Schur and solves; FP64 residual,
+                           gradient H^T W r, assembly of b_hat and update; optional
+                           FP64 refinement of the boundary solve                 */
 /* start modes */
 #define MASE_START_FLAT     0   /* Vm = 1, Va = 0                               */
 #define MASE_START_X0       1   /* x0 given to mase_solve                        */
@@ -108,7 +109,7 @@ typedef struct {
     int32_t precision;   /* MASE_FP64 | MASE_MIXED                     */
     int32_t schedule;    /* MASE_PER_AREA | MASE_BATCHED               */
     int32_t use_graph;   /* 1: replay each iteration as a CUDA graph    */
-    int32_t refine;      /* boundary refinement sweeps (MIXED), e.g. 1  */
+    int32_t refine;      /* boundary refinement sweeps (MIXED), 0..8    */
     int32_t threads;     /* threads per CTA of the area kernels, 0=auto */
     int32_t device;      /* CUDA device ordinal                         */
     void   *stream;      /* cudaStream_t, NULL = default stream         */
@@ -148,7 +149,9 @@ typedef struct {
     int32_t boundary_levels;                /* levels of the boundary factor */
 } mase_info;
 
-/* Default options: MIXED, BATCHED, graph on, 1 refinement sweep, device 0. */
+/* Default options: MIXED, BATCHED, graph on, no refinement sweep (each
+ * Gauss-Newton step is then an inexact Newton step; the FP64 residual and
+ * gradient fix the converged state), device 0. */
 void mase_default_options(mase_options *opt);
 
 /* Build a handle: validates the inputs, runs the one-time symbolic setup

@@ -82,6 +82,17 @@ def test_parity_small_grids(mase, name, precision, schedule):
     _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
 
 
+@pytest.mark.parametrize("refine", [1, 3])
+def test_parity_with_boundary_refinement(mase, refine):
+    """The optional FP64 refinement sweeps of the boundary solve (MIXED)."""
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 2, 3250)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED, refine=refine)
+    assert res.rc == mase.MASE_OK, res
+    _check(net, g, x, res, z, w, range(2))
+
+
 def test_parity_slack_on_boundary(mase):
     g = synth.make_grid("grid2869_k16", slack_on_boundary=True)
     net, Vm, Va, z, sig = problem(g, 2, 3300)
