@@ -109,6 +109,9 @@ struct mase_handle {
     DevBuf<unsigned long long> maxstep;
     int *h_n_active = nullptr;   // pinned
     size_t smem_local = 0, smem_back = 0, smem_bnd = 0;
+    // coordinator on 2-block clusters (the whole boundary factor on chip)
+    int bnd_cluster = 0;
+    size_t smem_bnd_cl = 0;
     long long fac_elems = 0, c_elems = 0, bh_elems = 0;
     // measurement function tables (canonical numbering)
     DevBuf<int> m_from, m_to, m_inc_beg, m_inc_br;

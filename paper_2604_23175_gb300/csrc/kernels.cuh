@@ -175,6 +175,31 @@ struct SplitStore {  // entries [split, ...) in shared memory, the rest in globa
     __device__ __forceinline__ RG *at(int off) const { return off >= split ? sm + (off - split) : g + off; }
 };
 
+template <class RG>
+struct ClusterStore {  // entries [split, ...) in cluster block 0's shared memory, the rest in block 1's
+    RG *p0;
+    RG *p1;
+    int split;
+    __device__ __forceinline__ RG *at(int off) const { return off >= split ? p0 + (off - split) : p1 + off; }
+};
+
+// The threads that run a level-scheduled factorisation or solve: one block,
+// or both blocks of a 2-block cluster working on one snapshot.
+struct BlockTeam {
+    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
+    __device__ __forceinline__ int nwarps() const { return blockDim.x >> 5; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct ClusterTeam {
+    int rank;
+    __device__ __forceinline__ int warp() const { return rank * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+    __device__ __forceinline__ int nwarps() const { return 2 * (blockDim.x >> 5); }
+    __device__ __forceinline__ void sync() const {
+        // full cluster barrier; orders shared-memory traffic of both blocks
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+};
+
 // Diagonal block of a supernode panel (w <= WB <= 32 columns), by one warp:
 // lane r holds row r, column values are broadcast by shuffles; then the
 // block's rhs is forward-solved the same way.
@@ -476,9 +501,10 @@ __device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS 
 // blocks, then the panel chunks, then the update units, each group spread over
 // the warps and closed by a block barrier.  Suits factors whose top levels are
 // wide (the boundary system) better than the dataflow.
-template <class RG, class RS, class ST>
-__device__ void factor_levels(const FacDev &F, const Tables &T, const ST &st, RS *y, int *err) {
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+template <class RG, class RS, class ST, class TM = BlockTeam>
+__device__ void factor_levels(const FacDev &F, const Tables &T, const ST &st, RS *y, int *err,
+                              const TM &tm = TM()) {
+    const int warp = tm.warp(), nw = tm.nwarps();
     const int4 *trec = T.task_rec + 4 * (long long)F.task_base;
     const int *lt = T.lev_tasks + F.levtask_base;
     const int *rel = T.rel + F.rel_base;
@@ -498,7 +524,7 @@ __device__ void factor_levels(const FacDev &F, const Tables &T, const ST &st, RS
                 task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3);
             }
         }
-        __syncthreads();
+        tm.sync();
     }
 }
 
@@ -512,10 +538,10 @@ __device__ __forceinline__ void factor_numeric(const FacDev &F, const Tables &T,
 // Forward solve L y = b with a factored storage, level by level: diagonal
 // blocks by one warp each, then the rhs updates of the rows below them in
 // 32-row chunks over all warps.  Must be called by every thread of the block.
-template <class RG, class RS, class ST>
-__device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS *y) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
-              nw = nt >> 5;
+template <class RG, class RS, class ST, class TM = BlockTeam>
+__device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS *y,
+                              const TM &tm = TM()) {
+    const int lane = threadIdx.x & 31, warp = tm.warp(), nw = tm.nwarps();
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
     const int *lev_chunks = T.lev_chunks + F.levchunk_base;
@@ -529,7 +555,7 @@ __device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS
             diag_block_any<RG, RS>(st.at(T.sn_off[s]), w, w + T.sn_nr[s], y + T.sn_c0[s], false,
                                    lane, nullptr);
         }
-        __syncthreads();
+        tm.sync();
         for (int k = lev_chunks[lev] + warp; k < lev_chunks[lev + 1]; k += nw) {
             const int4 r = crec[2 * k], r2 = crec[2 * k + 1];
             const RG *P = st.at(r.x);
@@ -541,17 +567,18 @@ __device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS
                 atomicAdd(y + rows[r2.y + row - w], -v);
             }
         }
-        __syncthreads();
+        tm.sync();
     }
 }
 
 // Backward solve L^T x = y over the internal supernodes, top level first.
 // y[n_int..] must hold the (already known) boundary unknowns; on return
 // y[0..n_int) holds the interior solution (Eq. backsub).
-template <class RG, class RS, class ST>
-__device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y) {
+template <class RG, class RS, class ST, class TM = BlockTeam>
+__device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y,
+                           const TM &tm = TM()) {
     constexpr unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = tm.warp(), nw = tm.nwarps();
     const int *sn_order = T.sn_order + F.sn_base;
     const int *lev_off = T.lev_off + F.levoff_base;
     const int *lev_chunks = T.lev_chunks + F.levchunk_base;
@@ -571,7 +598,7 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y
                 if (lane == 0) atomicAdd(y + r2.x + c, -v);
             }
         }
-        __syncthreads();
+        tm.sync();
         // (b) backward substitution with the diagonal block (lane r holds y_r)
         const int a = lev_off[lev], e = lev_off[lev + 1];
         for (int i = a + warp; i < e; i += nw) {
@@ -597,7 +624,7 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y
                 __syncwarp();
             }
         }
-        __syncthreads();
+        tm.sync();
     }
 }
 
@@ -839,6 +866,7 @@ struct BndDev {
     long long stride;     // storage elements per snapshot
     int split;            // storage entries from here on live in shared memory
     int smem_off_ctr;     // byte offset of the task counters (2 nsn + 1 ints)
+    int split_cl;         // 2-block cluster: entries [split_cl, ...) in block 0, the rest in block 1
     int smem_off_st;      // byte offset of the shared part of the storage
 };
 
@@ -866,7 +894,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
         for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i)
             v += fac[B.asm_abs[i] + (long long)s * B.asm_str[i]];
         *st.at(P) = v;
-        Am[P] = v;
+        if (refine) Am[P] = v;
     }
     for (int gi = tid; gi < nG; gi += nt) {
         double v = 0.0;
@@ -932,6 +960,107 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
         atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
         if (s_err) atomicOr(X.err + s, s_err);
     }
+}
+
+// The coordinator for one snapshot on a 2-block cluster: the boundary
+// factor lives in the shared memory of both blocks (distributed shared
+// memory), the vectors in block 0's; both blocks' warps share the level
+// schedule, with cluster barriers between task groups.
+template <class RG, class RS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
+    k_boundary_cl(Tables T, State X, BndDev B, const RG *__restrict__ fac,
+                  const double *__restrict__ bh, RG *bA, double *dxG, int refine) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_err;
+    const int rank = (int)__clusterRelativeBlockRank();
+    const int s = blockIdx.x >> 1;
+    if (!X.active[s]) return;   // both blocks of the cluster leave together
+    const ClusterTeam tm{rank};
+    const int tid = threadIdx.x, nt = blockDim.x, nG = B.n_gamma;
+    const int ct = rank * nt + tid, cn = 2 * nt;
+    if (tid == 0) s_err = 0;
+    tm.sync();   // both blocks are running before either touches the other's memory
+    unsigned char *sm0 = (unsigned char *)__cluster_map_shared_rank(smem, 0);
+    unsigned char *sm1 = (unsigned char *)__cluster_map_shared_rank(smem, 1);
+    double *bhat = (double *)sm0;
+    double *x = bhat + nG;
+    double *r = x + nG;
+    RS *y = (RS *)(r + nG);
+    const ClusterStore<RG> st{(RG *)(sm0 + B.smem_off_st), (RG *)sm1, B.split_cl};
+    RG *Am = bA + (long long)s * B.stride;
+    for (int P = ct; P < B.F.store_total; P += cn) {
+        RG v = RG(0);
+        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i)
+            v += fac[B.asm_abs[i] + (long long)s * B.asm_str[i]];
+        *st.at(P) = v;
+        if (refine) Am[P] = v;
+    }
+    for (int gi = ct; gi < nG; gi += cn) {
+        double v = 0.0;
+        for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i)
+            v += bh[B.rhs_abs[i] + (long long)s * B.rhs_str[i]];
+        bhat[gi] = v;
+        y[gi] = RS(v);
+    }
+    tm.sync();
+    factor_levels<RG, RS>(B.F, T, st, y, &s_err, tm);
+    back_solve<RG, RS>(B.F, T, st, y, tm);
+    for (int gi = ct; gi < nG; gi += cn) x[gi] = double(y[gi]);
+    tm.sync();
+    const int lane = tid & 31;
+    for (int it = 0; it < refine; ++it) {
+        // r = b_hat - S_Gamma x, FP64 accumulation over the stored lower triangle
+        for (int gi = ct; gi < nG; gi += cn) r[gi] = bhat[gi];
+        tm.sync();
+        for (int sn = tm.warp(); sn < B.F.nsn; sn += tm.nwarps()) {
+            const int sg = B.F.sn_base + sn;
+            const int w = T.sn_w[sg], R = T.sn_nr[sg], ld = w + R, c0 = T.sn_c0[sg];
+            const RG *P = Am + T.sn_off[sg];
+            const int *rows = T.rows + B.F.rows_base + T.sn_rows[sg];
+            for (int c = 0; c < w; ++c) {
+                const int col = c0 + c;
+                double accc = 0.0;
+                for (int rr = c + lane; rr < ld; rr += 32) {
+                    const int row = rr < w ? c0 + rr : rows[rr - w];
+                    const double a = double(P[(size_t)c * ld + rr]);
+                    if (row == col) {
+                        accc += a * x[col];
+                    } else {
+                        atomicAdd(r + row, -a * x[col]);
+                        accc += a * x[row];
+                    }
+                }
+                accc = warp_sum(accc);
+                if (lane == 0) atomicAdd(r + col, -accc);
+            }
+        }
+        tm.sync();
+        for (int gi = ct; gi < nG; gi += cn) y[gi] = RS(r[gi]);
+        tm.sync();
+        solve_forward<RG, RS>(B.F, T, st, y, tm);
+        back_solve<RG, RS>(B.F, T, st, y, tm);
+        for (int gi = ct; gi < nG; gi += cn) x[gi] += double(y[gi]);
+        tm.sync();
+    }
+    double mx = 0.0;
+    bool bad = false;
+    for (int gi = ct; gi < nG; gi += cn) {
+        const double d = x[gi];
+        dxG[(long long)s * nG + gi] = d;
+        const long long at = (long long)s * X.N + B.bvar_ibus[gi];
+        if (B.bvar_isT[gi]) X.xT[at] += d;
+        else X.xV[at] += d;
+        if (!isfinite(d)) bad = true;
+        mx = fmax(mx, fabs(d));
+    }
+    if (bad) atomicOr(X.err + s, 2);
+    mx = block_max(mx, red);
+    if (tid == 0) {
+        atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
+        if (s_err) atomicOr(X.err + s, s_err);
+    }
+    tm.sync();   // neither block leaves while the other may still use its shared memory
 }
 
 // ---------------------------------------------------------------------------

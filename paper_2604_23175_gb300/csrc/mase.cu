@@ -128,6 +128,8 @@ void setup_attrs(mase_handle *h) {
     cudaFuncSetAttribute(k_back<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
     cudaFuncSetAttribute(k_boundary<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          h->smem_limit);
+    cudaFuncSetAttribute(k_boundary_cl<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         h->smem_limit);
 }
 
 State make_state(mase_handle *h) {
@@ -176,9 +178,14 @@ int enqueue_step(mase_handle *h, int *launches) {
     }
     mark(h, 1);
     if (h->bnd.n_gamma > 0) {
-        k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
-                                                      (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p,
-                                                      h->opt.precision == MASE_MIXED ? h->opt.refine : 0);
+        const int refine = h->opt.precision == MASE_MIXED ? h->opt.refine : 0;
+        if (h->bnd_cluster)
+            k_boundary_cl<RG, RS><<<2 * S, nt, h->smem_bnd_cl, st>>>(h->T, X, h->bnd, fac, h->bh.p,
+                                                                   (RG *)h->bA.p, h->dxG.p, refine);
+        else
+            k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
+                                                          (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p,
+                                                          refine);
         ++*launches;
     }
     mark(h, 2);
@@ -348,6 +355,15 @@ int build(mase_handle *h) {
         bd.split = split;
         bd.smem_off_st = (int)vec;
         h->smem_bnd = vec + (size_t)(B.F.store_total - split) * sizeof(RG);
+        // MIXED: a 2-block cluster holds the rest of the factor in its second
+        // block's shared memory when it fits
+        bd.split_cl = split;
+        h->bnd_cluster = 0;
+        if (h->opt.precision == MASE_MIXED && (size_t)split * sizeof(RG) <= (size_t)h->smem_limit &&
+            2 * (size_t)nS <= 65535) {
+            h->bnd_cluster = 1;
+            h->smem_bnd_cl = std::max(h->smem_bnd, (size_t)split * sizeof(RG));
+        }
     }
     // instance list: areas by descending work, snapshots innermost
     std::vector<int> ord(K);
