@@ -66,8 +66,8 @@ extern "C" {
 /* precision modes */
 #define MASE_FP64   0   /* every step in FP64 (the plain comparator)               */
 #define MASE_MIXED  1   /* FP32 gain, factor, Schur and solves; FP64 residual,
-                           gradient H^T W r, assembly of b_hat and update; optional
-                           FP64 refinement of the boundary solve                 */
+                           gradient H^T W r, assembly of b_hat, refinement of the
+                           boundary solve and update                             */
 /* start modes */
 #define MASE_START_FLAT     0   /* Vm = 1, Va = 0                               */
 #define MASE_START_X0       1   /* x0 given to mase_solve                        */
@@ -149,9 +149,10 @@ typedef struct {
     int32_t boundary_levels;                /* levels of the boundary factor */
 } mase_info;
 
-/* Default options: MIXED, BATCHED, graph on, no refinement sweep (each
- * Gauss-Newton step is then an inexact Newton step; the FP64 residual and
- * gradient fix the converged state), device 0. */
+/* Default options: MIXED, BATCHED, graph on, one FP64 refinement sweep of the
+ * boundary solve, device 0.  (refine = 0 makes each Gauss-Newton step an
+ * inexact Newton step; the FP64 residual and gradient still fix the
+ * converged state.) */
 void mase_default_options(mase_options *opt);
 
 /* Build a handle: validates the inputs, runs the one-time symbolic setup

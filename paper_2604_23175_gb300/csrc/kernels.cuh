@@ -870,6 +870,70 @@ struct BndDev {
     int smem_off_st;      // byte offset of the shared part of the storage
 };
 
+// r -= S x for the boundary system S (symmetric, lower part stored in
+// supernode layout, FP32 or FP64 values, FP64 accumulation): one task per
+// diagonal block and per 32-row chunk below it, spread over the team's warps.
+// A chunk (lane = row) adds its rows' products in registers and the column
+// sums by a transpose-reduction of the 32 per-lane columns (31 exchanges).
+template <class RG>
+__device__ __noinline__ void residual_chunk(const RG *P, int w, int ld, int row0, int c0,
+                                            const int *rws, const double *x, double *r) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, row = row0 + lane;
+    const bool ok = row < ld;
+    const int grow = ok ? rws[row - w] : 0;
+    const double xr = ok ? x[grow] : 0.0;
+    double v[32];
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const double a = (ok && c < w) ? double(P[(size_t)c * ld + row]) : 0.0;
+        acc += a * (c < w ? x[c0 + c] : 0.0);
+        v[c] = a * xr;
+    }
+    if (ok) atomicAdd(r + grow, -acc);
+    // after the exchange at distance d a lane keeps the half of its columns
+    // whose bit d matches its own; in the end lane c holds column c's sum
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const bool up = (lane & d) != 0;
+#pragma unroll
+        for (int k = 0; k < d; ++k) {
+            const double send = up ? v[k] : v[k + d];
+            const double keep = up ? v[k + d] : v[k];
+            v[k] = keep + __shfl_xor_sync(FULL, send, d);
+        }
+    }
+    if (lane < w) atomicAdd(r + c0 + lane, -v[0]);
+}
+
+template <class RG, class TM>
+__device__ void boundary_residual(const FacDev &F, const Tables &T, const RG *Am, const double *x,
+                                  double *r, const TM &tm) {
+    const int lane = threadIdx.x & 31;
+    const int4 *crec = T.chunk_rec + 2 * (long long)F.chunk_base;
+    const int nch = T.lev_chunks[F.levchunk_base + F.nlev];
+    const int *rows = T.rows + F.rows_base;
+    for (int k = tm.warp(); k < F.nsn + nch; k += tm.nwarps()) {
+        if (k < F.nsn) {
+            const int sg = F.sn_base + k;
+            const int w = T.sn_w[sg], ld = w + T.sn_nr[sg], c0 = T.sn_c0[sg];
+            const RG *P = Am + T.sn_off[sg];
+            if (lane < w) {
+                double acc = 0.0;
+                for (int c = 0; c < w; ++c) {
+                    const RG a = c <= lane ? P[(size_t)c * ld + lane] : P[(size_t)lane * ld + c];
+                    acc += double(a) * x[c0 + c];
+                }
+                atomicAdd(r + c0 + lane, -acc);
+            }
+        } else {
+            const int4 q = crec[2 * (k - F.nsn)], q2 = crec[2 * (k - F.nsn) + 1];
+            residual_chunk<RG>(Am + q.x, q.y, q.z, q.w, q2.x, rows + q2.y, x, r);
+        }
+    }
+}
+
 template <class RG, class RS>
 __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ areas, Tables T,
                                                   State X, BndDev B, const RG *__restrict__ fac,
@@ -912,29 +976,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
         // r = b_hat - S_Gamma x, FP64 accumulation over the stored lower triangle
         for (int gi = tid; gi < nG; gi += nt) r[gi] = bhat[gi];
         __syncthreads();
-        const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-        for (int sn = warp; sn < B.F.nsn; sn += nw) {
-            const int sg = B.F.sn_base + sn;
-            const int w = T.sn_w[sg], R = T.sn_nr[sg], ld = w + R, c0 = T.sn_c0[sg];
-            const RG *P = Am + T.sn_off[sg];
-            const int *rows = T.rows + B.F.rows_base + T.sn_rows[sg];
-            for (int c = 0; c < w; ++c) {
-                const int col = c0 + c;
-                double accc = 0.0;
-                for (int rr = c + lane; rr < ld; rr += 32) {
-                    const int row = rr < w ? c0 + rr : rows[rr - w];
-                    const double a = double(P[(size_t)c * ld + rr]);
-                    if (row == col) {
-                        accc += a * x[col];
-                    } else {
-                        atomicAdd(r + row, -a * x[col]);
-                        accc += a * x[row];
-                    }
-                }
-                accc = warp_sum(accc);
-                if (lane == 0) atomicAdd(r + col, -accc);
-            }
-        }
+        boundary_residual<RG>(B.F, T, Am, x, r, BlockTeam());
         __syncthreads();
         for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
         __syncthreads();
@@ -1008,33 +1050,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     back_solve<RG, RS>(B.F, T, st, y, tm);
     for (int gi = ct; gi < nG; gi += cn) x[gi] = double(y[gi]);
     tm.sync();
-    const int lane = tid & 31;
     for (int it = 0; it < refine; ++it) {
         // r = b_hat - S_Gamma x, FP64 accumulation over the stored lower triangle
         for (int gi = ct; gi < nG; gi += cn) r[gi] = bhat[gi];
         tm.sync();
-        for (int sn = tm.warp(); sn < B.F.nsn; sn += tm.nwarps()) {
-            const int sg = B.F.sn_base + sn;
-            const int w = T.sn_w[sg], R = T.sn_nr[sg], ld = w + R, c0 = T.sn_c0[sg];
-            const RG *P = Am + T.sn_off[sg];
-            const int *rows = T.rows + B.F.rows_base + T.sn_rows[sg];
-            for (int c = 0; c < w; ++c) {
-                const int col = c0 + c;
-                double accc = 0.0;
-                for (int rr = c + lane; rr < ld; rr += 32) {
-                    const int row = rr < w ? c0 + rr : rows[rr - w];
-                    const double a = double(P[(size_t)c * ld + rr]);
-                    if (row == col) {
-                        accc += a * x[col];
-                    } else {
-                        atomicAdd(r + row, -a * x[col]);
-                        accc += a * x[row];
-                    }
-                }
-                accc = warp_sum(accc);
-                if (lane == 0) atomicAdd(r + col, -accc);
-            }
-        }
+        boundary_residual<RG>(B.F, T, Am, x, r, tm);
         tm.sync();
         for (int gi = ct; gi < nG; gi += cn) y[gi] = RS(r[gi]);
         tm.sync();

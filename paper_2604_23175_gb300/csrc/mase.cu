@@ -635,7 +635,7 @@ void mase_default_options(mase_options *o) {
     o->precision = MASE_MIXED;
     o->schedule = MASE_BATCHED;
     o->use_graph = 1;
-    o->refine = 0;
+    o->refine = 1;
     o->threads = 0;
     o->device = 0;
     o->stream = nullptr;

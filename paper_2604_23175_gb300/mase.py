@@ -213,7 +213,7 @@ class Estimator:
     """One handle: a network, its partition and a batch of n_snap snapshots."""
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
-                 schedule=BATCHED, use_graph=True, refine=0, threads=0, device=0, stream=None,
+                 schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
                  profile=False):
         self.lib = load()
         net, part, keep = _network(grid)

@@ -82,9 +82,10 @@ def test_parity_small_grids(mase, name, precision, schedule):
     _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
 
 
-@pytest.mark.parametrize("refine", [1, 3])
-def test_parity_with_boundary_refinement(mase, refine):
-    """The optional FP64 refinement sweeps of the boundary solve (MIXED)."""
+@pytest.mark.parametrize("refine", [0, 3])
+def test_parity_refinement_sweeps(mase, refine):
+    """MIXED without the FP64 refinement of the boundary solve (an inexact
+    Newton step each iteration) and with three sweeps."""
     g = synth.make_grid("grid2869_k16")
     net, Vm, Va, z, sig = problem(g, 2, 3250)
     w = wls.weights(sig)
