@@ -470,6 +470,9 @@ __device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS 
         if (lane == 0) t = atomicAdd(next, 1);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntask) break;
+        // the record a warp will take about one round of grabs later, into L1
+        if (lane == 0 && t + 16 < ntask)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(trec + 4 * (t + 16)));
         const int4 q0 = trec[4 * t], q1 = trec[4 * t + 1], q2 = trec[4 * t + 2], q3 = trec[4 * t + 3];
         if (lane == 0 && q0.z > 0) {
             const volatile int *c = ctr + q0.y;

@@ -88,10 +88,11 @@ void build_tasks(SymFactor &F, int nwarps, bool level_sched) {
     for (int s = 0; s < nsn; ++s) {
         const int w = F.sn_w[s], ld = w + F.sn_nr[s];
         d_of[s] = (int)tk.size();
-        tk.push_back({0, s, 0, 400.0 + 350.0 * w});
+        // estimated cycles (fitted to per-task timings of the area kernel on GB300)
+        tk.push_back({0, s, 0, 300.0 + 550.0 * w});
         for (int r0 = w; r0 < ld; r0 += 32) {
             c_of[s].push_back((int)tk.size());
-            tk.push_back({1, s, r0, 300.0 + 200.0 * w});
+            tk.push_back({1, s, r0, 300.0 + 300.0 * w});
             ++nchunk[s];
         }
     }
@@ -111,8 +112,9 @@ void build_tasks(SymFactor &F, int nwarps, bool level_sched) {
             u_rhs[u] = e;
         }
         const int tid = (int)tk.size();
-        const double iters = std::ceil((R - j) / 32.0);
-        tk.push_back({2, s, (int)u, 300.0 + iters * (w * (20.0 + 5.0 * nj) + 150.0)});
+        const double passes = std::ceil((R - j) / 96.0);
+        const double mc = std::min(3.0, std::ceil((R - j) / 32.0));
+        tk.push_back({2, s, (int)u, 2500.0 + passes * w * std::max(50.0, 60.0 * nj + 110.0 * mc - 250.0)});
         u_of[s].push_back(tid);
         if (t >= 0) {
             u_into[t].push_back(tid);
