@@ -574,6 +574,35 @@ __device__ void solve_forward(const FacDev &F, const Tables &T, const ST &st, RS
     }
 }
 
+// Column sums sum_rows P[c][row] * xi of one 32-row chunk of a panel (lane =
+// row, w <= WB columns): a transpose-reduction of the lanes' WB products (the
+// lanes exchange halves of their columns at distances WB/2 .. 1, WB - 1
+// exchanges in all, after folding the two half-warps when WB = 16).  Lane c
+// returns column c.
+template <class RG, class RS, int WB>
+__device__ __forceinline__ RS chunk_colsum(const RG *P, int w, int ld, int row, RS xi, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool ok = row < ld;
+    RS v[WB];
+#pragma unroll
+    for (int c = 0; c < WB; ++c) v[c] = (ok && c < w) ? RS(P[(size_t)c * ld + row]) * xi : RS(0);
+    if (WB == 16) {
+#pragma unroll
+        for (int c = 0; c < WB; ++c) v[c] += __shfl_xor_sync(FULL, v[c], 16);
+    }
+#pragma unroll
+    for (int d = WB / 2; d >= 1; d >>= 1) {
+        const bool up = (lane & d) != 0;
+#pragma unroll
+        for (int k = 0; k < d; ++k) {
+            const RS send = up ? v[k] : v[k + d];
+            const RS keep = up ? v[k + d] : v[k];
+            v[k] = keep + __shfl_xor_sync(FULL, send, d);
+        }
+    }
+    return v[0];
+}
+
 // Backward solve L^T x = y over the internal supernodes, top level first.
 // y[n_int..] must hold the (already known) boundary unknowns; on return
 // y[0..n_int) holds the interior solution (Eq. backsub).
@@ -595,11 +624,10 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y
             const RG *P = st.at(r.x);
             const int w = r.y, ld = r.z, row = r.w + lane;
             const RS xi = row < ld ? y[rows[r2.y + row - w]] : RS(0);
-            for (int c = 0; c < w; ++c) {
-                RS v = row < ld ? RS(P[(size_t)c * ld + row]) * xi : RS(0);
-                v = warp_sum(v);
-                if (lane == 0) atomicAdd(y + r2.x + c, -v);
-            }
+            RS sum;
+            if (w <= 16) sum = chunk_colsum<RG, RS, 16>(P, w, ld, row, xi, lane);
+            else sum = chunk_colsum<RG, RS, 32>(P, w, ld, row, xi, lane);
+            if (lane < w) atomicAdd(y + r2.x + lane, -sum);
         }
         tm.sync();
         // (b) backward substitution with the diagonal block (lane r holds y_r)
