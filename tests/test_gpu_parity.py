@@ -82,6 +82,20 @@ def test_parity_small_grids(mase, name, precision, schedule):
     _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
 
 
+@pytest.mark.parametrize("threads", [128, 256])
+def test_parity_fewer_warps_without_graphs(mase, threads):
+    """The task lists are scheduled for 16 warps; fewer warps per block must
+    give the same estimates (any warp count preserves the topological order),
+    and so must stepping without CUDA graphs."""
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 2, 3260)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED, threads=threads,
+                  use_graph=False)
+    assert res.rc == mase.MASE_OK, res
+    _check(net, g, x, res, z, w, range(2))
+
+
 @pytest.mark.parametrize("refine", [0, 3])
 def test_parity_refinement_sweeps(mase, refine):
     """MIXED without the FP64 refinement of the boundary solve (an inexact
