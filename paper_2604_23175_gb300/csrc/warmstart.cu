@@ -736,7 +736,7 @@ void backward(mase_handle *h, WarmStart &W, Workspace &ws) {
 }
 
 // moments and normalised features/targets of a chunk of internal-layout data
-int ingest_chunk(mase_handle *h, WarmStart &W, const double *z_can, const double *x_can, int n,
+int ingest_chunk(mase_handle *h, const double *z_can, const double *x_can, int n,
                  bool host, DevBuf<double> &zc, DevBuf<double> &zi, DevBuf<double> &xc,
                  DevBuf<double> &xv, DevBuf<double> &xt) {
     cudaStream_t st = h->stream;
@@ -860,7 +860,7 @@ int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32
     WK(cudaMemsetAsync(os2.p, 0, W->OS * sizeof(double), st));
     for (int s0 = 0; s0 < n; s0 += chunk) {
         const int c = std::min(chunk, n - s0);
-        rc = ingest_chunk(h, *W, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        rc = ingest_chunk(h, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
         if (rc != MASE_OK) return rc;
         k_moments_rows<<<grid_for(W->FS), 256, 0, st>>>(zi.p, M, W->feat_src.p, W->FS, c, fs1.p, fs2.p);
         k_moments_out<<<grid_for(W->OS), 256, 0, st>>>(xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M,
@@ -876,7 +876,7 @@ int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32
     WK(Tall.alloc((size_t)n * W->OS));
     for (int s0 = 0; s0 < n; s0 += chunk) {
         const int c = std::min(chunk, n - s0);
-        rc = ingest_chunk(h, *W, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        rc = ingest_chunk(h, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
         if (rc != MASE_OK) return rc;
         k_features<<<grid_for((long long)c * W->FS), 256, 0, st>>>(
             zi.p, M, nullptr, W->feat_src.p, W->feat_mu.p, W->feat_sd.p, W->FS, c,
