@@ -901,6 +901,41 @@ struct BndDev {
     int smem_off_st;      // byte offset of the shared part of the storage
 };
 
+// Gathers S_Gamma = sum_k E_k^T S_b^k E_k (Eq. global_assembly) into the
+// boundary factor storage (and the refinement's copy Am when given): entry P
+// sums the stored S_b entries listed in asm_beg[P] .. asm_beg[P+1].  Four
+// entries per thread at a time, so that their first source loads overlap.
+template <class RG, class ST>
+__device__ __forceinline__ void assemble_boundary(const BndDev &B, const RG *__restrict__ fac, int s,
+                                                  const ST &st, RG *Am, int t0, int nt) {
+    const long long so = (long long)s;
+    for (int P0 = t0; P0 < B.F.store_total; P0 += 4 * nt) {
+        int i0[4], i1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int P = P0 + u * nt;
+            const bool ok = P < B.F.store_total;
+            i0[u] = ok ? B.asm_beg[P] : 0;
+            i1[u] = ok ? B.asm_beg[P + 1] : 0;
+        }
+        RG v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = i0[u] < i1[u] ? fac[B.asm_abs[i0[u]] + so * B.asm_str[i0[u]]] : RG(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            for (int i = i0[u] + 1; i < i1[u]; ++i) v[u] += fac[B.asm_abs[i] + so * B.asm_str[i]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int P = P0 + u * nt;
+            if (P < B.F.store_total) {
+                *st.at(P) = v[u];
+                if (Am) Am[P] = v[u];
+            }
+        }
+    }
+}
+
 // r -= S x for the boundary system S (symmetric, lower part stored in
 // supernode layout, FP32 or FP64 values, FP64 accumulation): one task per
 // diagonal block and per 32-row chunk below it, spread over the team's warps.
@@ -984,13 +1019,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
     const SplitStore<RG> st{bst + (long long)s * B.stride, (RG *)(smem + B.smem_off_st), B.split};
     RG *Am = bA + (long long)s * B.stride;
     if (tid == 0) s_err = 0;
-    for (int P = tid; P < B.F.store_total; P += nt) {
-        RG v = RG(0);
-        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i)
-            v += fac[B.asm_abs[i] + (long long)s * B.asm_str[i]];
-        *st.at(P) = v;
-        if (refine) Am[P] = v;
-    }
+    assemble_boundary<RG>(B, fac, s, st, refine ? Am : nullptr, tid, nt);
     for (int gi = tid; gi < nG; gi += nt) {
         double v = 0.0;
         for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i)
@@ -1062,13 +1091,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     RS *y = (RS *)(r + nG);
     const ClusterStore<RG> st{(RG *)(sm0 + B.smem_off_st), (RG *)sm1, B.split_cl};
     RG *Am = bA + (long long)s * B.stride;
-    for (int P = ct; P < B.F.store_total; P += cn) {
-        RG v = RG(0);
-        for (int i = B.asm_beg[P]; i < B.asm_beg[P + 1]; ++i)
-            v += fac[B.asm_abs[i] + (long long)s * B.asm_str[i]];
-        *st.at(P) = v;
-        if (refine) Am[P] = v;
-    }
+    assemble_boundary<RG>(B, fac, s, st, refine ? Am : nullptr, ct, cn);
     for (int gi = ct; gi < nG; gi += cn) {
         double v = 0.0;
         for (int i = B.rhs_beg[gi]; i < B.rhs_beg[gi + 1]; ++i)
