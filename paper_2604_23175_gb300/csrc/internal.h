@@ -102,6 +102,7 @@ struct mase_handle {
     DevBuf<uint8_t> mask_int, mask_stage;
     bool has_mask = false, has_z = false;
     DevBuf<int> zperm, bus_of_ibus;
+    DevBuf<double> h_flat;   // h(x) at the flat start, internal row order
     // work buffers
     DevBuf<unsigned char> fac, cvec, bst, bA;
     DevBuf<double> bh, dxG, J, laststep, xbuf;

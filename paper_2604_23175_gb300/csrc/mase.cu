@@ -752,6 +752,21 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
             br[fill[fr[l]]++] = l;
             br[fill[to[l]]++] = l;
         }
+        // measurement values at the flat start (Vm = 1, Va = 0), internal row
+        // order: Vm rows 1, active power rows 0, a reactive flow is -b_c/2 at
+        // its end and a reactive injection the sum over the incident branches
+        {
+            std::vector<double> hc((size_t)3 * N + 4 * (size_t)L, 0.0), hi(M);
+            for (int i = 0; i < N; ++i) hc[i] = 1.0;
+            for (int l = 0; l < L; ++l) {
+                hc[2 * (size_t)N + fr[l]] -= bh[l];
+                hc[2 * (size_t)N + to[l]] -= bh[l];
+                hc[3 * (size_t)N + (size_t)L + l] = -bh[l];       // Qf
+                hc[3 * (size_t)N + 3 * (size_t)L + l] = -bh[l];   // Qt
+            }
+            for (int r = 0; r < M; ++r) hi[r] = hc[h->S.zperm[r]];
+            CK(h->h_flat.upload(hi, st));
+        }
         CK(h->m_from.upload(fr, st));
         CK(h->m_to.upload(to, st));
         CK(h->m_g.upload(g, st));

@@ -407,6 +407,25 @@ __global__ void k_pick_start(const double *Jl, const double *Jf, const double *x
     }
 }
 
+// J = sum_r w_r (z_r - h_r(x_flat))^2 per snapshot, from the closed-form
+// flat-start measurement values (one block row per snapshot, FP64)
+__global__ void k_flat_objective(const double *__restrict__ z, const double *__restrict__ W,
+                                 const uint8_t *__restrict__ mask, const double *__restrict__ hflat,
+                                 int M, double *J) {
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    const double *zs = z + (long long)s * M;
+    const uint8_t *ms = mask ? mask + (long long)s * M : nullptr;
+    double acc = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x) {
+        const double w = ms ? (ms[r] ? W[r] : 0.0) : W[r];
+        const double d = zs[r] - hflat[r];
+        acc += w * d * d;
+    }
+    const double t = mase_dev::block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(J + s, t);
+}
+
 inline int grid_for(long long n, int threads = 256) {
     long long g = (n + threads - 1) / threads;
     return (int)std::min<long long>(std::max<long long>(g, 1), 4096);
@@ -788,7 +807,11 @@ int learned_start(mase_handle *h, int *launches) {
     WK(cudaMemsetAsync(W->Jl.p, 0, S * sizeof(double), st));
     WK(cudaMemsetAsync(W->Jf.p, 0, S * sizeof(double), st));
     launch_objective(h, h->xV2.p, h->xT2.p, W->Jl.p, launches);
-    launch_objective(h, h->xV.p, h->xT.p, W->Jf.p, launches);
+    // the flat start's objective needs no evaluation pass: h(x_flat) is fixed
+    k_flat_objective<<<dim3(8, S), 256, 0, st>>>(h->z_int.p, h->W.p,
+                                                 h->has_mask ? h->mask_int.p : nullptr,
+                                                 h->h_flat.p, M, W->Jf.p);
+    ++*launches;
     k_pick_start<<<grid_for((long long)S * N), 256, 0, st>>>(W->Jl.p, W->Jf.p, h->xV2.p, h->xT2.p,
                                                             h->xV.p, h->xT.p, N, S, W->picked.p);
     launches[0] += 1;
