@@ -246,7 +246,7 @@ int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const doubl
  * activations are BF16 with FP32 accumulation on the tensor cores; master
  * weights and AdamW moments are FP32.  With MASE_START_LEARNED, mase_solve
  * keeps the proposal per snapshot only where its objective J is below the
- * flat start's, so Gauss-Newton remains the judge of the proposal. */
+ * flat start's, so Gauss-Newton has the last word on the proposal. */
 typedef struct {
     int32_t  hidden;        /* width of the three hidden layers, multiple of 8 (512)   */
     int32_t  epochs;        /* passes over the training set                            */

@@ -4,7 +4,7 @@
 // accumulated in FP32 on the tensor cores, and the master weights and AdamW
 // moments are FP32.  The networks are trained on states the estimator itself
 // produced; in mase_solve the proposal is kept per snapshot only where it has
-// a lower WLS objective than the flat start, so Gauss-Newton stays the judge.
+// a lower WLS objective than the flat start, so Gauss-Newton has the last word.
 // The paper has no learned component; this file is the warm-start part of
 // the build.
 #include <cuda_bf16.h>
