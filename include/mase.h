@@ -115,6 +115,10 @@ typedef struct {
     void   *stream;      /* cudaStream_t, NULL = default stream         */
     int32_t profile;     /* 1: time each stage with CUDA events into
                             mase_stats.stage_ms                          */
+    int32_t inner_iters; /* 0..8 local Gauss-Newton steps per area with the
+                            boundary state held fixed before each condensed
+                            step (Eq. local_wls); 0 = the exact condensed
+                            step alone, whose iterates equal centralised GN */
 } mase_options;
 
 /* Per-solve results.  Arrays are host arrays of n_snap entries supplied by

@@ -106,6 +106,7 @@ struct mase_handle {
     // work buffers
     DevBuf<unsigned char> fac, cvec, bst, bA;
     DevBuf<double> bh, dxG, J, laststep, xbuf;
+    DevBuf<double> dx_zero;   // a zero boundary step for the inner local iterations
     DevBuf<int> active, err, iters, status, n_active;
     DevBuf<unsigned long long> maxstep;
     int *h_n_active = nullptr;   // pinned

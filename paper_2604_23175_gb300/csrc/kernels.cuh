@@ -1238,6 +1238,14 @@ __global__ void k_finalize(State X, int *iters, int *status, double *laststep,
     if (threadIdx.x == 0) *n_active = cnt;
 }
 
+// clears the step norm and the objective left by inner local iterations
+__global__ void k_clear_step(State X) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < X.S; s += gridDim.x * blockDim.x) {
+        X.maxstep[s] = 0ull;
+        X.J[s] = 0.0;
+    }
+}
+
 __global__ void k_reset(State X, int *iters, int *status, double *laststep) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < X.S; s += gridDim.x * blockDim.x) {
         X.active[s] = 1;

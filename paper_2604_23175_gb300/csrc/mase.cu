@@ -158,24 +158,59 @@ inline void mark(mase_handle *h, int i) {
 }
 
 template <class RG, class RS>
-int enqueue_step(mase_handle *h, int *launches) {
-    State X = make_state(h);
-    cudaStream_t st = h->stream;
+void launch_local(mase_handle *h, const State &X, RG *fac, RS *cv, int *launches) {
     const int S = h->n_snap, K = h->S.K, nt = h->threads;
-    RG *fac = (RG *)h->fac.p;
-    RS *cv = (RS *)h->cvec.p;
-    mark(h, 0);
     if (h->opt.schedule == MASE_BATCHED) {
-        k_local<RG, RS><<<K * S, nt, h->smem_local, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1,
-                                                         MODE_FULL, fac, cv, h->bh.p);
+        k_local<RG, RS><<<K * S, nt, h->smem_local, h->stream>>>(h->d_areas.p, h->T, X, h->d_inst.p,
+                                                                -1, MODE_FULL, fac, cv, h->bh.p);
         ++*launches;
     } else {
         for (int k = 0; k < K; ++k) {
-            k_local<RG, RS><<<S, nt, h->areas_h[k].smem_bytes, st>>>(
+            k_local<RG, RS><<<S, nt, h->areas_h[k].smem_bytes, h->stream>>>(
                 h->d_areas.p, h->T, X, nullptr, k, MODE_FULL, fac, cv, h->bh.p);
             ++*launches;
         }
     }
+}
+
+template <class RG, class RS>
+void launch_back(mase_handle *h, const State &X, const RG *fac, const RS *cv, const double *dxG,
+                 int *launches) {
+    const int S = h->n_snap, K = h->S.K;
+    if (h->opt.schedule == MASE_BATCHED) {
+        k_back<RG, RS><<<K * S, kBackThreads, h->smem_back, h->stream>>>(
+            h->d_areas.p, h->T, X, h->d_inst.p, -1, fac, cv, dxG, h->bnd.n_gamma);
+        ++*launches;
+    } else {
+        for (int k = 0; k < K; ++k) {
+            const size_t sm = (size_t)h->areas_h[k].back_smem_bytes;
+            k_back<RG, RS><<<S, kBackThreads, sm, h->stream>>>(h->d_areas.p, h->T, X, nullptr, k, fac,
+                                                               cv, dxG, h->bnd.n_gamma);
+            ++*launches;
+        }
+    }
+}
+
+template <class RG, class RS>
+int enqueue_step(mase_handle *h, int *launches) {
+    State X = make_state(h);
+    cudaStream_t st = h->stream;
+    const int S = h->n_snap, nt = h->threads;
+    RG *fac = (RG *)h->fac.p;
+    RS *cv = (RS *)h->cvec.p;
+    mark(h, 0);
+    // local Gauss-Newton steps with the boundary held fixed (Eq. local_wls):
+    // the area pass, then the interior recovery with a zero boundary step
+    for (int q = 0; q < h->opt.inner_iters; ++q) {
+        launch_local<RG, RS>(h, X, fac, cv, launches);
+        launch_back<RG, RS>(h, X, fac, cv, h->dx_zero.p, launches);
+    }
+    if (h->opt.inner_iters > 0) {
+        // the outer step alone decides convergence
+        k_clear_step<<<(S + 255) / 256, 256, 0, st>>>(X);
+        ++*launches;
+    }
+    launch_local<RG, RS>(h, X, fac, cv, launches);
     mark(h, 1);
     if (h->bnd.n_gamma > 0) {
         const int refine = h->opt.precision == MASE_MIXED ? h->opt.refine : 0;
@@ -189,18 +224,7 @@ int enqueue_step(mase_handle *h, int *launches) {
         ++*launches;
     }
     mark(h, 2);
-    if (h->opt.schedule == MASE_BATCHED) {
-        k_back<RG, RS><<<K * S, kBackThreads, h->smem_back, st>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1, fac,
-                                                       cv, h->dxG.p, h->bnd.n_gamma);
-        ++*launches;
-    } else {
-        for (int k = 0; k < K; ++k) {
-            const size_t sm = (size_t)h->areas_h[k].back_smem_bytes;
-            k_back<RG, RS><<<S, kBackThreads, sm, st>>>(h->d_areas.p, h->T, X, nullptr, k, fac, cv, h->dxG.p,
-                                             h->bnd.n_gamma);
-            ++*launches;
-        }
-    }
+    launch_back<RG, RS>(h, X, fac, cv, h->dxG.p, launches);
     mark(h, 3);
     return MASE_OK;
 }
@@ -458,6 +482,8 @@ int build(mase_handle *h) {
     CK(h->bst.alloc((size_t)std::max(1, B.F.store_total) * nS * sizeof(RG)));
     CK(h->bA.alloc((size_t)std::max(1, B.F.store_total) * nS * sizeof(RG)));
     CK(h->dxG.alloc((size_t)std::max(1, B.n_gamma) * nS));
+    CK(h->dx_zero.alloc((size_t)std::max(1, B.n_gamma) * nS));
+    CK(cudaMemsetAsync(h->dx_zero.p, 0, (size_t)std::max(1, B.n_gamma) * nS * sizeof(double), st));
     setup_attrs<RG, RS>(h);
     // info
     mase_info &I = h->info;
@@ -640,6 +666,7 @@ void mase_default_options(mase_options *o) {
     o->device = 0;
     o->stream = nullptr;
     o->profile = 0;
+    o->inner_iters = 0;
 }
 
 const char *mase_status_str(int code) {
@@ -670,6 +697,8 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     if (h->opt.schedule != MASE_PER_AREA && h->opt.schedule != MASE_BATCHED)
         return set_err(MASE_EINVAL, "bad schedule");
     if (h->opt.refine < 0 || h->opt.refine > 8) return set_err(MASE_EINVAL, "bad refine count");
+    if (h->opt.inner_iters < 0 || h->opt.inner_iters > 8)
+        return set_err(MASE_EINVAL, "bad inner iteration count");
     int threads = h->opt.threads ? h->opt.threads : 512;
     if (threads < 64 || threads > 512 || threads % 32) return set_err(MASE_EINVAL, "bad threads");
     h->threads = threads;

@@ -44,7 +44,7 @@ class Measurements(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
-                ("stream", C.c_void_p), ("profile", C.c_int32)]
+                ("stream", C.c_void_p), ("profile", C.c_int32), ("inner_iters", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -214,7 +214,7 @@ class Estimator:
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
                  schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
-                 profile=False):
+                 profile=False, inner_iters=0):
         self.lib = load()
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -223,6 +223,7 @@ class Estimator:
         opt.refine, opt.threads, opt.device = refine, threads, device
         opt.stream = C.c_void_p(stream) if stream else None
         opt.profile = int(bool(profile))
+        opt.inner_iters = int(inner_iters)
         meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
         h = C.c_void_p()
         rc = self.lib.mase_create(C.byref(net), C.byref(part), C.byref(meas), C.byref(opt), C.byref(h))

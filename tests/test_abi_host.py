@@ -49,7 +49,7 @@ def test_status_strings_and_defaults(mase):
     assert mase.status_str(0) == "MASE_OK"
     assert mase.status_str(-2) == "MASE_EUNOBSERVABLE"
     o = mase.default_options()
-    assert o.precision == mase.MIXED and o.schedule == mase.BATCHED and o.refine == 1
+    assert o.precision == mase.MIXED and o.schedule == mase.BATCHED and o.refine == 1 and o.inner_iters == 0
 
 
 @pytest.mark.parametrize("name", ["grid300_k4", "grid2869_k16", "grid9241_k32"])

@@ -82,6 +82,19 @@ def test_parity_small_grids(mase, name, precision, schedule):
     _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
 
 
+@pytest.mark.parametrize("precision,schedule", [("MIXED", "BATCHED"), ("FP64", "PER_AREA")])
+def test_parity_inner_local_iterations(mase, precision, schedule):
+    """Two local Gauss-Newton steps per area with the boundary fixed before each
+    condensed step (Eq. local_wls) change the path, not the WLS estimate."""
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 2, 3270)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=getattr(mase, precision),
+                  schedule=getattr(mase, schedule), inner_iters=2)
+    assert res.rc == mase.MASE_OK, res
+    _check(net, g, x, res, z, w, range(2))
+
+
 @pytest.mark.parametrize("threads", [128, 256])
 def test_parity_fewer_warps_without_graphs(mase, threads):
     """The task lists are scheduled for 16 warps; fewer warps per block must
