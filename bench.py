@@ -52,6 +52,8 @@ def parse():
                     help="estimator-solved snapshots for the warm-start networks (0: flat start)")
     ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--snapshots", type=int, default=N_SNAP)
+    ap.add_argument("--areas", type=int, default=0,
+                    help="draw the workload's grid with this many areas instead (sweeps)")
     return ap.parse_args()
 
 
@@ -154,7 +156,17 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def workload_inputs(args):
     from paper_2604_23175_gb300 import synth
-    g = synth.make_grid(args.workload)
+    if args.areas:
+        # the workload's bus and branch counts drawn with another number of
+        # areas, sizes scaled like the 32-area case (150-450 buses, mean 289)
+        base = synth.SPECS[args.workload]
+        mean = base.n_bus / args.areas
+        spec = synth.GridSpec(f"{base.name}_k{args.areas}", base.n_bus, base.n_branch, args.areas,
+                              max(8, round(0.52 * mean)), round(1.56 * mean), base.ties_lo,
+                              base.ties_hi, base.extra_pairs, seed=base.seed)
+        g = synth.make_grid(spec)
+    else:
+        g = synth.make_grid(args.workload)
     Vm, Va = synth.make_states(g, args.snapshots, STATE_SEED)
     e = synth.make_noise(g, args.snapshots, NOISE_SEED)
     sig = synth.sigma_vector(g.n_bus, g.n_branch)
