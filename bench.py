@@ -52,6 +52,8 @@ def parse():
                     help="estimator-solved snapshots for the warm-start networks (0: flat start)")
     ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--snapshots", type=int, default=N_SNAP)
+    ap.add_argument("--family", default="", choices=["", "Pf", "Qf", "Pt", "Qt", "Pinj", "Qinj", "Vm"],
+                    help="drop one whole measurement family from every snapshot")
     ap.add_argument("--areas", type=int, default=0,
                     help="draw the workload's grid with this many areas instead (sweeps)")
     return ap.parse_args()
@@ -251,7 +253,13 @@ def run_ours(args, dist):
     est.measure(x_true, z_dev)
     z_dev += torch.tensor(e, device="cuda")
     z_host = z_dev.cpu().numpy().copy()
-    est.set_measurements(z_dev)
+    mask_dev, mask_pin = None, None
+    if args.family:
+        from paper_2604_23175_gb300 import synth
+        mh = synth.family_mask(g, args.family, N_SNAP)
+        mask_dev = torch.tensor(mh, device="cuda")
+        mask_pin = torch.from_numpy(mh).pin_memory()
+    est.set_measurements(z_dev, mask_dev)
     info = est.info()
     x_dev = torch.zeros((N_SNAP, 2 * N), dtype=torch.float64, device="cuda")
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -262,7 +270,7 @@ def run_ours(args, dist):
     last = {}
 
     def step():
-        est.set_measurements(z_dev)
+        est.set_measurements(z_dev, mask_dev)
         last["r"] = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
 
     # ---- learned warm start (untimed set-up): train the per-area networks on
@@ -292,7 +300,7 @@ def run_ours(args, dist):
         del Zs, Xs
         warm = {"trained": True, "samples": nb * N_SNAP, "epochs": args.train_epochs,
                 "final_loss": loss, "data_s": t1 - t0, "train_s": t2 - t1}
-        est.set_measurements(z_dev)
+        est.set_measurements(z_dev, mask_dev)
         # iterations from the flat, previous-snapshot and learned starts
         rf = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_dev)
         x_flat = x_dev.clone()
@@ -349,7 +357,7 @@ def run_ours(args, dist):
     pin_x = torch.zeros((N_SNAP, 2 * N), dtype=torch.float64).pin_memory()
 
     def step_e2e():
-        est.set_measurements(pin_z)
+        est.set_measurements(pin_z, mask_pin)
         est.solve(tol=TOL, max_iter=MAX_ITER, x_out=pin_x)
 
     e2e_times = time_steps(torch, step_e2e, max(3, args.steps // 2), 2, flush)
@@ -363,7 +371,7 @@ def run_ours(args, dist):
     cres = {}
 
     def step_cmp():
-        cmp.set_measurements(z_dev)
+        cmp.set_measurements(z_dev, mask_dev)
         cres["r"] = cmp.solve(tol=TOL, max_iter=MAX_ITER, x_out=x_fp64)
 
     if args.comparator_steps > 0:
@@ -401,12 +409,16 @@ def run_ours(args, dist):
     except Exception:
         pass
 
+    # the headline workload, or a sweep / profiling variant of it
+    variant = bool(args.workload != WORKLOAD or N_SNAP != 64 or args.areas or args.family)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD and N_SNAP == 64 else f"{args.workload} x{N_SNAP} snapshots (profiling case)", "n_bus": g.n_bus, "n_branch": g.n_branch,
+        "config": {"workload": WORKLOAD_DESC if not variant else
+                   f"{g.name} x{N_SNAP} snapshots" + (f", {args.family} rows dropped" if args.family else ""),
+                   "n_bus": g.n_bus, "n_branch": g.n_branch,
                    "n_area": g.n_area, "n_snap": N_SNAP, "precision": "mixed (FP32 gain/factor/Schur/solves, FP64 residual/gradient/boundary refinement/update)",
                    "schedule": "batched, CUDA graph per iteration",
                    "start": "learned (per-area MLP, judged against flat by J)" if warm["trained"] else "flat",
@@ -424,7 +436,8 @@ def run_ours(args, dist):
                                "back": stages[2] / args.steps, "bookkeeping": stages[3] / args.steps},
         "roofline": roof,
         "e2e": {"value": dist.world * N_SNAP / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(z_host.nbytes), "d2h_bytes_per_step": int(x_host.nbytes),
+                "h2d_bytes_per_step": int(z_host.nbytes) + (int(mask_pin.numel()) if mask_pin is not None else 0),
+                "d2h_bytes_per_step": int(x_host.nbytes),
                 "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clk,
