@@ -486,10 +486,16 @@ print(json.dumps({"seconds": dt, "iters": [r.iters for r in res], "J": [r.J for 
 
 
 def kernel_hash() -> str:
+    """Hash of the device code with comments and blank lines removed, so that
+    recorded counters stay attached to the code they were taken on."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("kernels.cuh",):
-        h.update(open(os.path.join(ROOT, "paper_2604_23175_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2604_23175_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = [ln.split("//", 1)[0].rstrip() for ln in src.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -414,7 +414,8 @@ __device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, con
 }
 
 // Task bodies are kept out of line so that each gets the whole register file
-// for its own tile (the 32-column diagonal block lives in 32 registers).
+// for its own tile (a diagonal tile of up to 16 columns lives in 16 registers
+// per lane) and no tile spills.
 template <class RG, class RS, class ST>
 __device__ __noinline__ void task_diag(const ST st, int off, int w, int ld, RS *yc, int *err) {
     diag_block_any<RG, RS>(st.at(off), w, ld, yc, true, threadIdx.x & 31, err);
