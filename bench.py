@@ -48,9 +48,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4, help="snapshots in the oracle sample")
     ap.add_argument("--comparator-steps", type=int, default=3)
     ap.add_argument("--workload", default=WORKLOAD, help="grid shape (smaller ones for profiling)")
-    ap.add_argument("--train-samples", type=int, default=16384,
+    ap.add_argument("--train-samples", type=int, default=32768,
                     help="estimator-solved snapshots for the warm-start networks (0: flat start)")
-    ap.add_argument("--train-epochs", type=int, default=30)
+    ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--snapshots", type=int, default=N_SNAP)
     ap.add_argument("--family", default="", choices=["", "Pf", "Qf", "Pt", "Qt", "Pinj", "Qinj", "Vm"],
                     help="drop one whole measurement family from every snapshot")
