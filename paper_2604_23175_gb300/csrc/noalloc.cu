@@ -101,29 +101,8 @@ __global__ void __launch_bounds__(512) k_coordinator_noalloc(Tables T, BndDev B,
     for (int it = 0; it < refine; ++it) {
         for (int gi = tid; gi < nG; gi += nt) r[gi] = bhat[gi];
         __syncthreads();
-        const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-        for (int sn = warp; sn < B.F.nsn; sn += nw) {
-            const int sg = B.F.sn_base + sn;
-            const int w = T.sn_w[sg], R = T.sn_nr[sg], ld = w + R, c0 = T.sn_c0[sg];
-            const RG *P = Am + T.sn_off[sg];
-            const int *rows = T.rows + B.F.rows_base + T.sn_rows[sg];
-            for (int c = 0; c < w; ++c) {
-                const int col = c0 + c;
-                double accc = 0.0;
-                for (int rr = c + lane; rr < ld; rr += 32) {
-                    const int row = rr < w ? c0 + rr : rows[rr - w];
-                    const double a = double(P[(size_t)c * ld + rr]);
-                    if (row == col) {
-                        accc += a * x[col];
-                    } else {
-                        atomicAdd(r + row, -a * x[col]);
-                        accc += a * x[row];
-                    }
-                }
-                accc = warp_sum(accc);
-                if (lane == 0) atomicAdd(r + col, -accc);
-            }
-        }
+        // r = b_hat - S_Gamma x, FP64 accumulation over the stored lower triangle
+        boundary_residual<RG>(B.F, T, Am, x, r, BlockTeam());
         __syncthreads();
         for (int gi = tid; gi < nG; gi += nt) y[gi] = RS(r[gi]);
         __syncthreads();

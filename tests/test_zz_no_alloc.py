@@ -85,6 +85,34 @@ def test_coordinator_noalloc_matches_solve_step(mase):
     est.close()
 
 
+def test_coordinator_noalloc_mixed_with_refinement(mase):
+    """MIXED handles factor S_Gamma in FP32 and refine the step once in FP64;
+    the step then agrees with the FP64 one to the FP32 factor's accuracy."""
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    S = 2
+    net, Vm, Va, z, sig = problem(g, S, 5200)
+    w = wls.weights(sig)
+    part = wls.partition(net_of(g), g.area_of_bus, g.n_area)
+    rng = np.random.Generator(np.random.PCG64(5201))
+    x0 = np.concatenate([1.0 + 0.01 * rng.standard_normal((S, g.n_bus)),
+                         0.02 * rng.standard_normal((S, g.n_bus))], axis=1)
+    x0[:, g.n_bus + g.slack] = 0.0
+    est = mase.Estimator(g, sig, S, z=z, precision=mase.FP64, schedule=mase.BATCHED)
+    x1 = np.zeros_like(x0)
+    est.solve(x0=np.ascontiguousarray(x0), tol=0.0, max_iter=1, x_out=x1, check=False)
+    est.close()
+    cols = wls.state_columns(net)
+    ref = (x1 - x0)[:, cols][:, part.gamma_cols]
+    Sflat, bflat = _condensed_blocks(net, part, z, w, x0)
+    mixed = mase.Estimator(g, sig, S, z=z, precision=mase.MIXED, schedule=mase.BATCHED, refine=1)
+    dx = torch.full((S, len(part.gamma_cols)), float("nan"), dtype=torch.float64, device="cuda")
+    mixed.coordinator_noalloc(torch.tensor(Sflat, device="cuda"), torch.tensor(bflat, device="cuda"), dx)
+    got = dx.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+    mixed.close()
+
+
 def test_coordinator_noalloc_rejects_oversized_request(mase):
     import torch
     g = synth.make_grid("grid9241_k32")
