@@ -66,7 +66,7 @@ def test_setup_counts_match_oracle_partition(mase, name):
 
 
 @pytest.mark.parametrize("name,slack_b", [("grid300_k4", False), ("grid2869_k16", False),
-                                           ("grid2869_k16", True)])
+                                           ("grid2869_k16", True), ("grid9241_k32", False)])
 def test_symbolic_setup_selfcheck(mase, name, slack_b):
     g = synth.make_grid(name, slack_on_boundary=slack_b)
     err = mase.selfcheck(g, seed=7)
