@@ -15,12 +15,12 @@
 namespace mase_internal {
 
 struct HostTables {
-    std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_rows, sn_order, item_off, lev_items, lev_off;
-    std::vector<int> rows, colbase, relbase, rel;
-    std::vector<int> locbus, qvarV, qvarT, own_q, own_gvv, own_ebeg, own_sbeg;
+    std::vector<int> sn_c0, sn_w, sn_nr, sn_off, sn_order, lev_off;
+    std::vector<int> rows, rel;
+    std::vector<int> locbus, qvarV, qvarT, own_q, own_gvv, own_ebeg;
     std::vector<int> end_qi, end_qj, end_own, end_var, end_gpos;
     std::vector<double> end_g, end_b, end_bh;
-    std::vector<int> slot_q, slot_ebeg, slot_ecnt, item_own, item_uv, item_pos, ebnd;
+    std::vector<int> item_pos, ebnd;
     std::vector<int> tasks, lev_tasks, item_rec, chunk_rec, lev_chunks;
 };
 
@@ -85,10 +85,10 @@ struct mase_handle {
     std::vector<AreaDev> areas_h;
     BndDev bnd{};
     DevBuf<AreaDev> d_areas;
-    DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_rows, t_sn_order, t_item_off, t_lev_items,
-        t_lev_off, t_rows, t_colbase, t_relbase, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
-        t_own_gvv, t_own_ebeg, t_own_sbeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
-        t_slot_q, t_slot_ebeg, t_slot_ecnt, t_item_own, t_item_uv, t_item_pos, t_ebnd,
+    DevBuf<int> t_sn_c0, t_sn_w, t_sn_nr, t_sn_off, t_sn_order,
+        t_lev_off, t_rows, t_rel, t_locbus, t_qvarV, t_qvarT, t_own_q,
+        t_own_gvv, t_own_ebeg, t_end_qi, t_end_qj, t_end_own, t_end_var, t_end_gpos,
+        t_item_pos, t_ebnd,
         t_tasks, t_lev_tasks, t_item_rec, t_chunk_rec, t_lev_chunks;
     DevBuf<double> t_end_g, t_end_b, t_end_bh;
     DevBuf<int> b_asm_beg, b_asm_area, b_asm_off, b_rhs_beg, b_rhs_area, b_rhs_lv, b_bvar_ibus,

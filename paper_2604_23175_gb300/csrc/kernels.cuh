@@ -28,7 +28,6 @@ struct FacDev {
     int n_int, n_bnd, nsn, nlev;
     int store_int, store_total, off_B, max_w;
     int sn_base;       // per-supernode arrays
-    int lev_base;      // lev_items
     int levoff_base;   // lev_off (nlev + 1 entries)
     int rows_base;     // rows / colbase / relbase
     int rel_base;      // rel
@@ -43,7 +42,7 @@ struct FacDev {
 struct AreaDev {
     FacDev F;
     int nb_int, nb_loc, n_own, n_ends, n_slots, n_items;
-    int bus_base, own_base, own1_base, end_base, slot_base, item_base, ebnd_base;
+    int bus_base, own_base, own1_base, end_base, item_base, ebnd_base;
     int zrow_base;
     int in_smem;
     int off_g, off_y, off_bus, off_end, off_inj, off_self, off_st;   // dynamic smem byte offsets
@@ -56,15 +55,14 @@ struct AreaDev {
 };
 
 struct Tables {
-    const int *sn_c0, *sn_w, *sn_nr, *sn_off, *sn_rows, *sn_order, *item_off;
-    const int *lev_items, *lev_off;
-    const int *rows, *colbase, *relbase, *rel;
+    const int *sn_c0, *sn_w, *sn_nr, *sn_off, *sn_order;
+    const int *lev_off;
+    const int *rows, *rel;
     const int *locbus, *qvarV, *qvarT;
-    const int *own_q, *own_gvv, *own_ebeg, *own_sbeg;
+    const int *own_q, *own_gvv, *own_ebeg;
     const int *end_qi, *end_qj, *end_own, *end_var, *end_gpos;
     const double *end_g, *end_b, *end_bh;
-    const int *slot_q, *slot_ebeg, *slot_ecnt;
-    const int *item_own, *item_uv, *item_pos;
+    const int *item_pos;
     const int *ebnd;
     const int4 *task_rec;   // 4 int4 per factorisation task
     const int *lev_tasks;   // level schedule: group boundaries of the task list

@@ -57,18 +57,12 @@ FacDev append_fac(HostTables &H, const mase::SymFactor &F) {
     app(H.sn_w, F.sn_w);
     app(H.sn_nr, F.sn_nr);
     app(H.sn_off, F.sn_off);
-    app(H.sn_rows, F.sn_rows);
     app(H.sn_order, F.sn_order);
-    app(H.item_off, F.item_off);
-    d.lev_base = (int)H.lev_items.size();
-    app(H.lev_items, F.lev_items);
     d.levoff_base = (int)H.lev_off.size();
     if (F.lev_off.empty()) H.lev_off.push_back(0);
     else app(H.lev_off, F.lev_off);
     d.rows_base = (int)H.rows.size();
     app(H.rows, F.rows);
-    app(H.colbase, F.colbase);
-    app(H.relbase, F.relbase);
     d.rel_base = (int)H.rel.size();
     app(H.rel, F.rel);
     d.task_base = (int)(H.tasks.size() / 16);
@@ -280,7 +274,6 @@ int build(mase_handle *h) {
         app(H.own_gvv, A.own_gvv);
         d.own1_base = (int)H.own_ebeg.size();
         app(H.own_ebeg, A.own_ebeg);
-        app(H.own_sbeg, A.own_sbeg);
         d.end_base = (int)H.end_qi.size();
         app(H.end_qi, A.end_qi);
         app(H.end_qj, A.end_qj);
@@ -290,13 +283,7 @@ int build(mase_handle *h) {
         app(H.end_g, A.end_g);
         app(H.end_b, A.end_b);
         app(H.end_bh, A.end_bh);
-        d.slot_base = (int)H.slot_q.size();
-        app(H.slot_q, A.slot_q);
-        app(H.slot_ebeg, A.slot_ebeg);
-        app(H.slot_ecnt, A.slot_ecnt);
-        d.item_base = (int)H.item_own.size();
-        app(H.item_own, A.item_own);
-        app(H.item_uv, A.item_uv);
+        d.item_base = (int)(H.item_pos.size() / 4);
         app(H.item_pos, A.item_pos);
         app(H.item_rec, A.item_rec);
         d.ebnd_base = (int)H.ebnd.size();
@@ -400,14 +387,13 @@ int build(mase_handle *h) {
     // uploads
 #define UP(buf, vec) CK(h->buf.upload(H.vec, st))
     UP(t_sn_c0, sn_c0); UP(t_sn_w, sn_w); UP(t_sn_nr, sn_nr); UP(t_sn_off, sn_off);
-    UP(t_sn_rows, sn_rows); UP(t_sn_order, sn_order); UP(t_item_off, item_off);
-    UP(t_lev_items, lev_items); UP(t_lev_off, lev_off); UP(t_rows, rows); UP(t_colbase, colbase);
-    UP(t_relbase, relbase); UP(t_rel, rel); UP(t_locbus, locbus); UP(t_qvarV, qvarV);
+    UP(t_sn_order, sn_order);
+    UP(t_lev_off, lev_off); UP(t_rows, rows);
+    UP(t_rel, rel); UP(t_locbus, locbus); UP(t_qvarV, qvarV);
     UP(t_qvarT, qvarT); UP(t_own_q, own_q); UP(t_own_gvv, own_gvv); UP(t_own_ebeg, own_ebeg);
-    UP(t_own_sbeg, own_sbeg); UP(t_end_qi, end_qi); UP(t_end_qj, end_qj); UP(t_end_own, end_own);
+    UP(t_end_qi, end_qi); UP(t_end_qj, end_qj); UP(t_end_own, end_own);
     UP(t_end_var, end_var); UP(t_end_gpos, end_gpos); UP(t_end_g, end_g); UP(t_end_b, end_b);
-    UP(t_end_bh, end_bh); UP(t_slot_q, slot_q); UP(t_slot_ebeg, slot_ebeg);
-    UP(t_slot_ecnt, slot_ecnt); UP(t_item_own, item_own); UP(t_item_uv, item_uv);
+    UP(t_end_bh, end_bh);
     UP(t_item_pos, item_pos); UP(t_ebnd, ebnd);
 #undef UP
     CK(h->b_asm_beg.upload(B.asm_beg, st));
@@ -454,16 +440,15 @@ int build(mase_handle *h) {
     CK(h->d_inst.upload(h->inst_h, st));
     Tables &T = h->T;
     T.sn_c0 = h->t_sn_c0.p; T.sn_w = h->t_sn_w.p; T.sn_nr = h->t_sn_nr.p; T.sn_off = h->t_sn_off.p;
-    T.sn_rows = h->t_sn_rows.p; T.sn_order = h->t_sn_order.p; T.item_off = h->t_item_off.p;
-    T.lev_items = h->t_lev_items.p; T.lev_off = h->t_lev_off.p; T.rows = h->t_rows.p;
-    T.colbase = h->t_colbase.p; T.relbase = h->t_relbase.p; T.rel = h->t_rel.p;
+    T.sn_order = h->t_sn_order.p;
+    T.lev_off = h->t_lev_off.p; T.rows = h->t_rows.p;
+    T.rel = h->t_rel.p;
     T.locbus = h->t_locbus.p; T.qvarV = h->t_qvarV.p; T.qvarT = h->t_qvarT.p;
     T.own_q = h->t_own_q.p; T.own_gvv = h->t_own_gvv.p; T.own_ebeg = h->t_own_ebeg.p;
-    T.own_sbeg = h->t_own_sbeg.p; T.end_qi = h->t_end_qi.p; T.end_qj = h->t_end_qj.p;
+    T.end_qi = h->t_end_qi.p; T.end_qj = h->t_end_qj.p;
     T.end_own = h->t_end_own.p; T.end_var = h->t_end_var.p; T.end_gpos = h->t_end_gpos.p;
     T.end_g = h->t_end_g.p; T.end_b = h->t_end_b.p; T.end_bh = h->t_end_bh.p;
-    T.slot_q = h->t_slot_q.p; T.slot_ebeg = h->t_slot_ebeg.p; T.slot_ecnt = h->t_slot_ecnt.p;
-    T.item_own = h->t_item_own.p; T.item_uv = h->t_item_uv.p; T.item_pos = h->t_item_pos.p;
+    T.item_pos = h->t_item_pos.p;
     T.ebnd = h->t_ebnd.p;
     CK(h->t_tasks.upload(H.tasks.empty() ? std::vector<int>(16, 0) : H.tasks, st));
     T.task_rec = reinterpret_cast<const int4 *>(h->t_tasks.p);
