@@ -500,14 +500,11 @@ SymResult build_symbolic(const BusSystem &sys, double relax_alpha, int relax_wma
     F.lev_off.assign(nlev + 1, 0);
     for (int s = 0; s < nsn; ++s) ++F.lev_off[level[s] + 1];
     for (int l = 0; l < nlev; ++l) F.lev_off[l + 1] += F.lev_off[l];
-    F.item_off.assign(nsn, 0);
     F.lev_items.assign(nlev, 0);
     for (int l = 0; l < nlev; ++l) {
         int acc = 0;
         for (int i = F.lev_off[l]; i < F.lev_off[l + 1]; ++i) {
-            int s = F.sn_order[i];
-            long long R = F.sn_nr[s];
-            F.item_off[i] = acc;
+            long long R = F.sn_nr[F.sn_order[i]];
             acc += (int)(R * (R + 1) / 2 + R);
         }
         F.lev_items[l] = acc;

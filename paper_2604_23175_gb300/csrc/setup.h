@@ -33,7 +33,6 @@ struct SymFactor {
     std::vector<int> rel;                // relative row positions in target supernodes
     std::vector<int> lev_off;            // supernodes of level l: sn_order[lev_off[l]..lev_off[l+1])
     std::vector<int> sn_order;
-    std::vector<int> item_off;           // per sn_order position: first update item within its level
     std::vector<int> lev_items;          // per level: update items (pairs + rhs rows)
     // column units of the update phase: unit u covers target columns
     // unit_j[u] .. unit_j[u] + unit_nj[u] (at most kUnitCols) of supernode
