@@ -108,13 +108,22 @@ typedef struct {
 typedef struct {
     int32_t precision;   /* MASE_FP64 | MASE_MIXED                     */
     int32_t schedule;    /* MASE_PER_AREA | MASE_BATCHED               */
-    int32_t use_graph;   /* 1: replay each iteration as a CUDA graph    */
+    int32_t use_graph;   /* 1: run the Gauss-Newton loop as one CUDA graph
+                            with a device-side loop (no host round trip per
+                            step); 0: launch each step from the host      */
     int32_t refine;      /* boundary refinement sweeps (MIXED), 0..8    */
     int32_t threads;     /* threads per CTA of the area kernels, 0=auto */
     int32_t device;      /* CUDA device ordinal                         */
     void   *stream;      /* cudaStream_t, NULL = default stream         */
-    int32_t profile;     /* 1: time each stage with CUDA events into
-                            mase_stats.stage_ms                          */
+    int32_t profile;     /* 1: step from the host (use_graph is ignored) and
+                            time each stage's kernels with CUDA events on
+                            the library's stream; mase_stats.stage_ms[0..3]
+                            then hold those event times                  */
+    int32_t wait_polls;  /* unsatisfied polls after which a device-side
+                            dependency wait of the area factorisation gives
+                            up (snapshot status MASE_SNAP_DEVICE); 0 = the
+                            default (4194304 polls, about 0.2 s).  Small
+                            values exist to exercise that error path.     */
     int32_t inner_iters; /* 0..8 local Gauss-Newton steps per area with the
                             boundary state held fixed before each condensed
                             step (Eq. local_wls); 0 = the exact condensed
@@ -128,10 +137,18 @@ typedef struct {
     int32_t *status;      /* MASE_SNAP_* per snapshot                           */
     double  *J;           /* r^T W r at the returned state, per snapshot        */
     double  *max_step;    /* max |dx| of the last step, per snapshot            */
-    double   stage_ms[4]; /* device time of the area kernel (evaluation, accumulation,
-                             condensation), the coordinator, the back-substitution
-                             and the bookkeeping, summed over the solve's steps
-                             (0 unless options.profile)                          */
+    double   stage_ms[7]; /* where solve_ms went, in ms: [0] area kernel (evaluation,
+                             accumulation, condensation), [1] coordinator, [2] back-
+                             substitution, [3] bookkeeping, each summed over the steps
+                             from device clocks (first block start to last block end
+                             of the stage's launches), or from CUDA events around the
+                             stage's kernels with options.profile; [4] learned start (inference
+                             and its judge); [5] the rest outside the loop (reset,
+                             state in/out, objective pass, result copies); [6] time
+                             inside the loop outside the stages' kernels (launch gaps,
+                             and the per-step host round trip when use_graph = 0).
+                             The seven sum to solve_ms.                           */
+    double   solve_ms;       /* wall time of the solve on the library's stream    */
     int32_t  total_launches; /* kernels launched by the solve                   */
     int32_t  steps;          /* Gauss-Newton steps run for the batch (max over snapshots) */
 } mase_stats;
@@ -151,6 +168,10 @@ typedef struct {
     int32_t max_area_store;                 /* largest per-area factor storage (entries) */
     int32_t boundary_store;                 /* boundary-system factor storage (entries) */
     int32_t boundary_levels;                /* levels of the boundary factor */
+    int64_t coord_S_elems;                  /* sum over areas of nb(k)(nb(k)+1)/2: packed
+                                               Schur-block entries of one snapshot */
+    int64_t coord_b_elems;                  /* sum over areas of nb(k): condensed rhs
+                                               entries of one snapshot */
 } mase_info;
 
 /* Default options: MIXED, BATCHED, graph on, one FP64 refinement sweep of the
@@ -210,38 +231,41 @@ int mase_selfcheck(const mase_network *net, const mase_partition *part, uint64_t
 /* Message of the last mase_analyze / mase_selfcheck failure on this thread. */
 const char *mase_analyze_error(void);
 
-/* Coordinator step without device allocation (the paper has no counterpart;
- * it serves callers that cannot call cudaMalloc when they need the step:
- * code running while another thread captures a CUDA graph in global capture
- * mode, where cudaMalloc is refused; real-time loops that cannot take the
- * device-wide synchronisation cudaMalloc implies; hosts whose device memory
- * belongs to another allocator).  Given the condensed blocks of every area and
- * snapshot it assembles S_Gamma and b_hat_Gamma, factors, refines (MASE_MIXED
- * handles) and solves, like the coordinator inside mase_solve, and writes the
- * boundary step.  It calls no cudaMalloc, cudaFree or allocating library
- * routine: its scratch (boundary factor storage, the assembled copy used by
- * the refinement, index tables and per-snapshot status words) is one static
- * device array of 64 MiB that every GPU which loads the library holds until
- * the process exits; requests needing more return MASE_EINVAL with the
- * required size in mase_last_error().  The first call on a device resolves the
- * array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  All calls share the array
+/* Coordinator step without device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot call cudaMalloc when they need
+ * the step - a host program whose device memory belongs to another allocator
+ * (a framework's caching pool, or one pool carved out at start-up) that allows
+ * no raw allocations beside it, or a latency-bound loop that must not take the
+ * device-wide synchronisation cudaMalloc and cudaFree can imply.  Given the
+ * condensed blocks of every area and snapshot it assembles S_Gamma and
+ * b_hat_Gamma, factors, refines (MASE_MIXED handles) and solves, like the
+ * coordinator inside mase_solve, and writes the boundary step.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its scratch (boundary
+ * factor storage, the assembled copy used by the refinement, index tables and
+ * per-snapshot status words) is one static device array of 64 MiB that every
+ * GPU which loads the library holds until the process exits; requests needing
+ * more return MASE_EINVAL with the required size in mase_last_error().  The
+ * first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current.  All calls share the array
  * and it keeps the last call's contents: calls that overlap on the GPU (two
- * handles or threads at once) race.  Everything the step reads is rewritten
- * by each call.
+ * handles or threads at once) race.  Everything the step reads is rewritten by
+ * each call.  The call returns after the step is complete.
  *
- * S_blocks (device, FP64): for area k = 0..K-1, then snapshot s = 0..S-1, the
- *   packed lower triangle (column-major: column c holds rows c..nb-1) of
- *   S_b^k(s), nb = nb(k) local boundary unknowns ordered by ascending bus id
- *   over the area's own boundary buses and the far terminals of its tie lines,
- *   Vm then Va per bus, the slack angle omitted.
- * b_blocks (device, FP64): for k, then s, b_hat_b^k(s) [nb(k)] in that order.
- * dx_gamma (device, FP64) [S][n_gamma]: x_Gamma order = ascending boundary bus
- *   id, Vm then Va per bus, slack angle omitted.
- * Returns MASE_OK, MASE_EINVAL (null/host pointers, size above the maximum),
- * MASE_EUNOBSERVABLE (non-positive pivot), MASE_ENONFINITE or MASE_EDEVICE. */
-int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const double *b_blocks,
-                             double *dx_gamma);
+ * S_blocks (device, FP64, n_S elements): for area k = 0..K-1, then snapshot
+ *   s = 0..S-1, the packed lower triangle (column-major: column c holds rows
+ *   c..nb-1) of S_b^k(s), nb = nb(k) local boundary unknowns ordered by
+ *   ascending bus id over the area's own boundary buses and the far terminals
+ *   of its tie lines, Vm then Va per bus, the slack angle omitted.
+ *   n_S must equal S * mase_info.coord_S_elems.
+ * b_blocks (device, FP64, n_b elements): for k, then s, b_hat_b^k(s) [nb(k)]
+ *   in that order; n_b must equal S * mase_info.coord_b_elems.
+ * dx_gamma (device, FP64, n_dx = S * n_gamma elements) [S][n_gamma]: x_Gamma
+ *   order = ascending boundary bus id, Vm then Va per bus, slack angle omitted.
+ * Returns MASE_OK, MASE_EINVAL (null/host pointers, element counts that differ
+ * from the handle's, size above the maximum), MASE_EUNOBSERVABLE (non-positive
+ * pivot), MASE_ENONFINITE or MASE_EDEVICE. */
+int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, int64_t n_S,
+                             const double *b_blocks, int64_t n_b, double *dx_gamma, int64_t n_dx);
 
 /* ---- learned warm start (not in the paper) ----------------------------------
  * One MLP per area maps the area's own measurement rows (normalised) to the
@@ -285,6 +309,18 @@ int mase_warmstart_load(mase_handle *h, const char *path);
  * mean((Y - T)^2); grads has the layout of params. */
 int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const float *params,
                    const float *X, const float *T, float *loss, float *grads);
+
+/* The optimiser of the warm-start training on its own, for checking: the
+ * library's AdamW kernel run `steps` times over n FP32 parameters w (host,
+ * updated in place) with the gradients grads[steps][n] and learning rates
+ * lr[steps] (host).  Moments start at zero; beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8 as in training; per step t: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, w <- w (1 - lr wd) - lr (m / (1-b1^t)) /
+ * (sqrt(v / (1-b2^t)) + eps).  m_out, v_out (FP32) and w_bf16_out (the BF16
+ * copy the networks compute with, as raw bits) may be NULL. */
+int mase_adamw_check(int64_t n, int32_t steps, const float *lr, float weight_decay,
+                     const float *grads, float *w, float *m_out, float *v_out,
+                     uint16_t *w_bf16_out);
 
 void mase_destroy(mase_handle *h);
 const char *mase_status_str(int code);

@@ -51,6 +51,8 @@ int mase_analyze(const mase_network *net, const mase_partition *part, mase_info 
         info->n_units += (int64_t)A.F.unit_sn.size();
         info->max_levels = std::max(info->max_levels, A.F.nlev());
         info->max_area_store = std::max(info->max_area_store, A.F.store_total);
+        info->coord_S_elems += (int64_t)A.n_bnd * (A.n_bnd + 1) / 2;
+        info->coord_b_elems += A.n_bnd;
     }
     info->boundary_store = S.B.F.store_total;
     info->boundary_levels = S.B.F.nlev();

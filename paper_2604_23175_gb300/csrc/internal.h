@@ -125,7 +125,14 @@ struct mase_handle {
     DevBuf<StopRule> stop;
     cudaStream_t user_stream = nullptr;   // caller's stream (NULL = legacy default stream)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaEvent_t ev_stage[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_solve[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_stage[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // options.profile
+    // device-side loop control and stage clocks
+    cudaGraphConditionalHandle loop_cond = 0;
+    DevBuf<unsigned long long> clk;
+    DevBuf<double> clk_acc;
+    DevBuf<int> steps_dev;
+    StopRule *h_stop = nullptr;   // pinned
     mase_info info{};
     mase_internal::WarmStart *ws = nullptr;   // learned warm start, if trained or loaded
     DevBuf<double> xV2, xT2;                  // learned start kept while the flat start is judged
@@ -135,8 +142,11 @@ struct mase_handle {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         if (h_n_active) cudaFreeHost(h_n_active);
+        if (h_stop) cudaFreeHost(h_stop);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        for (auto &e : ev_solve)
+            if (e) cudaEventDestroy(e);
         for (auto &e : ev_stage)
             if (e) cudaEventDestroy(e);
         if (stream) cudaStreamDestroy(stream);

@@ -69,6 +69,7 @@ struct Tables {
     const int4 *item_rec;   // 1 int4 per injection item
     const int4 *chunk_rec;  // 2 int4 per 32-row panel chunk
     const int *lev_chunks;
+    int wait_polls;         // polls of a dataflow wait before it gives up (error bit 4)
 };
 
 struct StopRule {
@@ -86,11 +87,27 @@ struct State {
     int *err;                    // [S] bit 1: non-SPD pivot, bit 2: non-finite, bit 4: a bounded wait gave up
     double *J;                   // [S]
     unsigned long long *maxstep; // [S] bit pattern of max |dx| (non-negative double)
+    unsigned long long *clk;     // stage clock of this launch: {first block start, last block end}
+                                 // in globaltimer ns, or null
 };
 
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Stage clocks: the first block of a launch to start and the last to finish
+// bound the stage's device time (called by thread 0; clk_end after the
+// block's last barrier).
+__device__ __forceinline__ void clk_begin(unsigned long long *clk) {
+    if (clk && threadIdx.x == 0) atomicMin(clk, gtimer());
+}
+__device__ __forceinline__ void clk_end(unsigned long long *clk) {
+    if (clk && threadIdx.x == 0) atomicMax(clk + 1, gtimer());
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -453,7 +470,7 @@ template <class RG, class RS, class ST>
 __device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS *y, int *ctr,
                              int *err) {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int kWaitLimit = 1 << 22;
+    const int wait_limit = T.wait_polls;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     const int nsn = F.nsn, ntask = F.n_tasks;
     for (int i = tid; i <= 2 * nsn; i += nt) ctr[i] = 0;
@@ -477,7 +494,7 @@ __device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS 
             const volatile int *c = ctr + q0.y;
             int it = 0;
             while (*c < q0.z) {
-                if (++it > kWaitLimit) {
+                if (++it >= wait_limit) {
                     atomicOr(err, 4);
                     break;
                 }
@@ -680,6 +697,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         s = ks.y;
     }
     if (mode == MODE_FULL && !X.active[s]) return;
+    clk_begin(X.clk);
     const AreaDev A = areas[k];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nv = A.F.n_int + A.F.n_bnd;
@@ -880,6 +898,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         atomicAdd(X.J + s, Js);
         if (s_err) atomicOr(X.err + s, s_err);
     }
+    clk_end(X.clk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1009,6 +1028,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
     __shared__ int s_err;
     const int s = blockIdx.x;
     if (!X.active[s]) return;
+    clk_begin(X.clk);
     const int tid = threadIdx.x, nt = blockDim.x, nG = B.n_gamma;
     double *bhat = (double *)smem;
     double *x = bhat + nG;
@@ -1061,6 +1081,7 @@ __global__ void __launch_bounds__(512) k_boundary(const AreaDev *__restrict__ ar
         atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
         if (s_err) atomicOr(X.err + s, s_err);
     }
+    clk_end(X.clk);
 }
 
 // The coordinator for one snapshot on a 2-block cluster: the boundary
@@ -1077,6 +1098,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     const int rank = (int)__clusterRelativeBlockRank();
     const int s = blockIdx.x >> 1;
     if (!X.active[s]) return;   // both blocks of the cluster leave together
+    clk_begin(X.clk);
     const ClusterTeam tm{rank};
     const int tid = threadIdx.x, nt = blockDim.x, nG = B.n_gamma;
     const int ct = rank * nt + tid, cn = 2 * nt;
@@ -1134,6 +1156,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
         if (s_err) atomicOr(X.err + s, s_err);
     }
     tm.sync();   // neither block leaves while the other may still use its shared memory
+    clk_end(X.clk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1156,6 +1179,7 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
         s = ks.y;
     }
     if (!X.active[s]) return;
+    clk_begin(X.clk);
     const AreaDev A = areas[k];
     const int tid = threadIdx.x, nt = blockDim.x;
     RS *y = (RS *)smem;
@@ -1187,6 +1211,7 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
     if (bad) atomicOr(X.err + s, 2);
     mx = block_max(mx, red);
     if (tid == 0) atomicMax(X.maxstep + s, (unsigned long long)__double_as_longlong(mx));
+    clk_end(X.clk);
 }
 
 // layout conversions (defined below, in the translation unit that includes
@@ -1202,8 +1227,19 @@ __global__ void k_state_out(double *__restrict__ x, const double *xV, const doub
 // ---------------------------------------------------------------------------
 // per-snapshot bookkeeping after a step
 // ---------------------------------------------------------------------------
+// Per-step clocks and loop control, kept on the device so that a solve can
+// run as one graph with a device-side loop.
+struct StepCtl {
+    unsigned long long *clk;   // [3][2] stage clocks of the area, coordinator and back kernels
+    double *acc;               // [4] ms summed over the solve: area, coordinator, back, bookkeeping
+    int *steps;                // Gauss-Newton steps run in this solve
+    int *n_active;             // snapshots still iterating after the last step
+};
+
 __global__ void k_finalize(State X, int *iters, int *status, double *laststep,
-                           const StopRule *__restrict__ rule, int *n_active) {
+                           const StopRule *__restrict__ rule, StepCtl ctl,
+                           cudaGraphConditionalHandle cond, int use_cond) {
+    const unsigned long long t0 = gtimer();
     const double tol = rule->tol;
     const int max_iter = rule->max_iter;
     __shared__ int cnt;
@@ -1234,7 +1270,18 @@ __global__ void k_finalize(State X, int *iters, int *status, double *laststep,
     }
     atomicAdd(&cnt, c);
     __syncthreads();
-    if (threadIdx.x == 0) *n_active = cnt;
+    if (threadIdx.x == 0) {
+        *ctl.n_active = cnt;
+        const int steps = ++*ctl.steps;
+        for (int i = 0; i < 3; ++i) {
+            const unsigned long long a = ctl.clk[2 * i], b = ctl.clk[2 * i + 1];
+            if (b > a) ctl.acc[i] += 1e-6 * double(b - a);
+            ctl.clk[2 * i] = ~0ull;
+            ctl.clk[2 * i + 1] = 0ull;
+        }
+        if (use_cond) cudaGraphSetConditional(cond, (cnt > 0 && steps < max_iter) ? 1u : 0u);
+        ctl.acc[3] += 1e-6 * double(gtimer() - t0);
+    }
 }
 
 // clears the step norm and the objective left by inner local iterations
@@ -1245,7 +1292,12 @@ __global__ void k_clear_step(State X) {
     }
 }
 
-__global__ void k_reset(State X, int *iters, int *status, double *laststep) {
+__global__ void k_reset(State X, int *iters, int *status, double *laststep, StepCtl ctl) {
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        if (threadIdx.x < 6) ctl.clk[threadIdx.x] = (threadIdx.x & 1) ? 0ull : ~0ull;
+        if (threadIdx.x < 4) ctl.acc[threadIdx.x] = 0.0;
+        if (threadIdx.x == 0) *ctl.steps = 0;
+    }
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < X.S; s += gridDim.x * blockDim.x) {
         X.active[s] = 1;
         X.err[s] = 0;

@@ -140,15 +140,27 @@ State make_state(mase_handle *h) {
     X.err = h->err.p;
     X.J = h->J.p;
     X.maxstep = h->maxstep.p;
+    X.clk = nullptr;
     return X;
 }
 
+StepCtl make_ctl(mase_handle *h) {
+    StepCtl c;
+    c.clk = h->clk.p;
+    c.acc = h->clk_acc.p;
+    c.steps = h->steps_dev.p;
+    c.n_active = h->n_active.p;
+    return c;
+}
+
 // One Gauss-Newton step for every active snapshot: local condensation,
-// coordinator, back-substitution, bookkeeping.
-// Stage boundaries are recorded as external event nodes so that they also
-// time the replays of a captured graph.
+// coordinator, back-substitution, bookkeeping.  Each stage's kernels carry a
+// device clock (first block start, last block end), which the bookkeeping
+// kernel sums per step, so stage times need no host events and also hold
+// inside a graph with a device-side loop.  With options.profile the host
+// steps the loop and CUDA events bracket the stages as well.
 inline void mark(mase_handle *h, int i) {
-    if (h->opt.profile) cudaEventRecordWithFlags(h->ev_stage[i], h->stream, cudaEventRecordExternal);
+    if (h->opt.profile) cudaEventRecord(h->ev_stage[i], h->stream);
 }
 
 template <class RG, class RS>
@@ -193,43 +205,83 @@ int enqueue_step(mase_handle *h, int *launches) {
     RG *fac = (RG *)h->fac.p;
     RS *cv = (RS *)h->cvec.p;
     mark(h, 0);
+    State Xa = X, Xc = X, Xb = X;
+    Xa.clk = h->clk.p;
+    Xc.clk = h->clk.p + 2;
+    Xb.clk = h->clk.p + 4;
     // local Gauss-Newton steps with the boundary held fixed (Eq. local_wls):
     // the area pass, then the interior recovery with a zero boundary step
     for (int q = 0; q < h->opt.inner_iters; ++q) {
-        launch_local<RG, RS>(h, X, fac, cv, launches);
-        launch_back<RG, RS>(h, X, fac, cv, h->dx_zero.p, launches);
+        launch_local<RG, RS>(h, Xa, fac, cv, launches);
+        launch_back<RG, RS>(h, Xb, fac, cv, h->dx_zero.p, launches);
     }
     if (h->opt.inner_iters > 0) {
         // the outer step alone decides convergence
         k_clear_step<<<(S + 255) / 256, 256, 0, st>>>(X);
         ++*launches;
     }
-    launch_local<RG, RS>(h, X, fac, cv, launches);
+    launch_local<RG, RS>(h, Xa, fac, cv, launches);
     mark(h, 1);
     if (h->bnd.n_gamma > 0) {
         const int refine = h->opt.precision == MASE_MIXED ? h->opt.refine : 0;
         if (h->bnd_cluster)
-            k_boundary_cl<RG, RS><<<2 * S, nt, h->smem_bnd_cl, st>>>(h->T, X, h->bnd, fac, h->bh.p,
+            k_boundary_cl<RG, RS><<<2 * S, nt, h->smem_bnd_cl, st>>>(h->T, Xc, h->bnd, fac, h->bh.p,
                                                                    (RG *)h->bA.p, h->dxG.p, refine);
         else
-            k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
+            k_boundary<RG, RS><<<S, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, Xc, h->bnd, fac, h->bh.p,
                                                           (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p,
                                                           refine);
         ++*launches;
     }
     mark(h, 2);
-    launch_back<RG, RS>(h, X, fac, cv, h->dxG.p, launches);
+    launch_back<RG, RS>(h, Xb, fac, cv, h->dxG.p, launches);
     mark(h, 3);
     return MASE_OK;
 }
 
-int enqueue_finalize(mase_handle *h, int *launches) {
+// Bookkeeping after a step.  Inside the solve graph it also sets the
+// condition of the device-side loop; stepping from the host, the host reads
+// the count of snapshots still iterating.
+int enqueue_finalize(mase_handle *h, int *launches, bool in_graph) {
     State X = make_state(h);
     k_finalize<<<1, 1024, 0, h->stream>>>(X, h->iters.p, h->status.p, h->laststep.p, h->stop.p,
-                                         h->n_active.p);
+                                         make_ctl(h), h->loop_cond, in_graph ? 1 : 0);
     ++*launches;
     mark(h, 4);
-    CK(cudaMemcpyAsync(h->h_n_active, h->n_active.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (!in_graph)
+        CK(cudaMemcpyAsync(h->h_n_active, h->n_active.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return MASE_OK;
+}
+
+// The Gauss-Newton loop as one graph: a while node whose body is one step
+// and whose condition the bookkeeping kernel sets (snapshots still active and
+// steps below max_iter); the condition starts at 1 on every launch.
+template <class RG, class RS>
+int build_loop_graph(mase_handle *h) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    h->graph = g;
+    CK(cudaGraphConditionalHandleCreate(&h->loop_cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h->loop_cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    int per_step = 0;
+    int rc = enqueue_step<RG, RS>(h, &per_step);
+    int rc2 = rc == MASE_OK ? enqueue_finalize(h, &per_step, true) : rc;
+    cudaGraph_t captured = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &captured);
+    if (rc != MASE_OK) return rc;
+    if (rc2 != MASE_OK) return rc2;
+    CK(ce);
+    h->graph_launches = per_step;
+    CK(cudaGraphInstantiate(&h->graph_exec, g, 0));
     return MASE_OK;
 }
 
@@ -336,6 +388,8 @@ int build(mase_handle *h) {
         h->info.max_area_store = std::max(h->info.max_area_store, A.F.store_total);
         max_vars = std::max(max_vars, nv);
         max_nb = std::max(max_nb, A.n_bnd);
+        h->info.coord_S_elems += (int64_t)A.n_bnd * (A.n_bnd + 1) / 2;
+        h->info.coord_b_elems += A.n_bnd;
     }
     h->fac_elems = fac_off;
     h->c_elems = c_off;
@@ -439,6 +493,8 @@ int build(mase_handle *h) {
     CK(h->d_areas.upload(ah, st));
     CK(h->d_inst.upload(h->inst_h, st));
     Tables &T = h->T;
+    // a dependency wait gives up after this many unsatisfied polls (~0.2 s by default)
+    T.wait_polls = h->opt.wait_polls > 0 ? h->opt.wait_polls : (1 << 22);
     T.sn_c0 = h->t_sn_c0.p; T.sn_w = h->t_sn_w.p; T.sn_nr = h->t_sn_nr.p; T.sn_off = h->t_sn_off.p;
     T.sn_order = h->t_sn_order.p;
     T.lev_off = h->t_lev_off.p; T.rows = h->t_rows.p;
@@ -508,6 +564,13 @@ int upload_measurements(mase_handle *h, const mase_measurements *meas) {
         h->has_z = true;
     }
     if (meas->mask) {
+        if (!h->has_mask && h->graph_exec) {
+            // the captured loop reads the mask pointer it was captured with
+            cudaGraphExecDestroy(h->graph_exec);
+            cudaGraphDestroy(h->graph);
+            h->graph_exec = nullptr;
+            h->graph = nullptr;
+        }
         if (!h->mask_int.p) {
             CK(h->mask_int.alloc(n));
             CK(h->mask_stage.alloc(n));
@@ -532,7 +595,10 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     const int N = h->S.N, nS = h->n_snap;
     int launches = 0;
     State X = make_state(h);
-    k_reset<<<(nS + 255) / 256, 256, 0, st>>>(X, h->iters.p, h->status.p, h->laststep.p);
+    // events: solve start, learned start begin/end, loop begin/end, solve end
+    cudaEvent_t *ev = h->ev_solve;
+    CK(cudaEventRecord(ev[0], st));
+    k_reset<<<(nS + 255) / 256, 256, 0, st>>>(X, h->iters.p, h->status.p, h->laststep.p, make_ctl(h));
     ++launches;
     if (x0) {
         const double *src = x0;
@@ -547,51 +613,46 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     ++launches;
     CK(cudaGetLastError());
-    if (!x0 && h->start_mode == MASE_START_LEARNED) {
+    CK(cudaEventRecord(ev[1], st));
+    const bool learned = !x0 && h->start_mode == MASE_START_LEARNED;
+    if (learned) {
         int rc = mase_internal::learned_start(h, &launches);
         if (rc != MASE_OK) return rc;
     }
-    int steps = 0;
-    double stage_ms[4] = {0, 0, 0, 0};
-    StopRule rule{tol, max_iter};
-    CK(cudaMemcpyAsync(h->stop.p, &rule, sizeof(rule), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-    for (int it = 0; it < max_iter; ++it) {
-        if (h->opt.use_graph) {
-            if (!h->graph_exec) {
-                int per_step = 0;
-                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                int rc = enqueue_step<RG, RS>(h, &per_step);
-                int rc2 = enqueue_finalize(h, &per_step);
-                cudaGraph_t g = nullptr;
-                cudaError_t ce = cudaStreamEndCapture(st, &g);
-                if (rc != MASE_OK) return rc;
-                if (rc2 != MASE_OK) return rc2;
-                CK(ce);
-                h->graph = g;
-                h->graph_launches = per_step;
-                CK(cudaGraphInstantiate(&h->graph_exec, g, 0));
-            }
-            CK(cudaGraphLaunch(h->graph_exec, st));
-            launches += h->graph_launches;
-        } else {
+    CK(cudaEventRecord(ev[2], st));
+    // the stop rule goes through pinned host memory: the previous solve has
+    // finished with it (every solve ends with a stream synchronisation)
+    h->h_stop->tol = tol;
+    h->h_stop->max_iter = max_iter;
+    CK(cudaMemcpyAsync(h->stop.p, h->h_stop, sizeof(StopRule), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ev[3], st));
+    const bool device_loop = h->opt.use_graph && !h->opt.profile;
+    double ev_acc[4] = {0, 0, 0, 0};
+    if (device_loop) {
+        if (!h->graph_exec) {
+            int rc = build_loop_graph<RG, RS>(h);
+            if (rc != MASE_OK) return rc;
+        }
+        CK(cudaGraphLaunch(h->graph_exec, st));
+    } else {
+        for (int it = 0; it < max_iter; ++it) {
             int rc = enqueue_step<RG, RS>(h, &launches);
             if (rc != MASE_OK) return rc;
-            rc = enqueue_finalize(h, &launches);
+            rc = enqueue_finalize(h, &launches, false);
             if (rc != MASE_OK) return rc;
-        }
-        CK(cudaStreamSynchronize(st));
-        CK(cudaGetLastError());
-        ++steps;
-        if (h->opt.profile) {
-            for (int i = 0; i < 4; ++i) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, h->ev_stage[i], h->ev_stage[i + 1]));
-                stage_ms[i] += ms;
+            CK(cudaStreamSynchronize(st));
+            CK(cudaGetLastError());
+            if (h->opt.profile) {
+                for (int i = 0; i < 4; ++i) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, h->ev_stage[i], h->ev_stage[i + 1]));
+                    ev_acc[i] += ms;
+                }
             }
+            if (*h->h_n_active == 0) break;
         }
-        if (*h->h_n_active == 0) break;
     }
+    CK(cudaEventRecord(ev[4], st));
     int rc = enqueue_objective<RG, RS>(h, &launches);
     if (rc != MASE_OK) return rc;
     if (x_out) {
@@ -606,12 +667,20 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     std::vector<int> iters(nS), status(nS);
     std::vector<double> J(nS), last(nS);
+    double acc[4] = {0, 0, 0, 0};
+    int steps = 0;
     CK(cudaMemcpyAsync(iters.data(), h->iters.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(status.data(), h->status.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(J.data(), h->J.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(last.data(), h->laststep.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(acc, h->clk_acc.p, sizeof(acc), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&steps, h->steps_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ev[5], st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    if (device_loop) launches += h->graph_launches * steps;
+    if (h->opt.profile)
+        for (int i = 0; i < 4; ++i) acc[i] = ev_acc[i];
     int ret = MASE_OK;
     for (int s = 0; s < nS; ++s) {
         if (status[s] == MASE_SNAP_MAX_ITER && ret == MASE_OK) ret = MASE_NOT_CONVERGED;
@@ -628,7 +697,20 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         }
         stats->total_launches = launches;
         stats->steps = steps;
-        for (int i = 0; i < 4; ++i) stats->stage_ms[i] = stage_ms[i];
+        float t_all = 0.f, t_pre = 0.f, t_ws = 0.f, t_stop = 0.f, t_loop = 0.f, t_post = 0.f;
+        CK(cudaEventElapsedTime(&t_all, ev[0], ev[5]));
+        CK(cudaEventElapsedTime(&t_pre, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&t_ws, ev[1], ev[2]));
+        CK(cudaEventElapsedTime(&t_stop, ev[2], ev[3]));
+        CK(cudaEventElapsedTime(&t_loop, ev[3], ev[4]));
+        CK(cudaEventElapsedTime(&t_post, ev[4], ev[5]));
+        for (int i = 0; i < 4; ++i) stats->stage_ms[i] = acc[i];
+        stats->stage_ms[4] = t_ws;
+        stats->stage_ms[5] = (double)t_pre + t_stop + t_post;
+        // what the loop spent outside its stages' kernels: launch gaps and,
+        // when stepping from the host, the round trip of every step
+        stats->stage_ms[6] = (double)t_loop - (acc[0] + acc[1] + acc[2] + acc[3]);
+        stats->solve_ms = t_all;
     }
     if (ret == MASE_EUNOBSERVABLE) set_err(ret, "non-positive pivot in an area or boundary factor");
     if (ret == MASE_ENONFINITE) set_err(ret, "non-finite step");
@@ -651,6 +733,7 @@ void mase_default_options(mase_options *o) {
     o->device = 0;
     o->stream = nullptr;
     o->profile = 0;
+    o->wait_polls = 0;
     o->inner_iters = 0;
 }
 
@@ -684,6 +767,7 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     if (h->opt.refine < 0 || h->opt.refine > 8) return set_err(MASE_EINVAL, "bad refine count");
     if (h->opt.inner_iters < 0 || h->opt.inner_iters > 8)
         return set_err(MASE_EINVAL, "bad inner iteration count");
+    if (h->opt.wait_polls < 0) return set_err(MASE_EINVAL, "bad wait_polls");
     int threads = h->opt.threads ? h->opt.threads : 512;
     if (threads < 64 || threads > 512 || threads % 32) return set_err(MASE_EINVAL, "bad threads");
     h->threads = threads;
@@ -705,6 +789,7 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    for (auto &e : h->ev_solve) CK(cudaEventCreate(&e));
     for (auto &e : h->ev_stage) CK(cudaEventCreate(&e));
     {
         int rc0 = join_in(h.get());
@@ -742,7 +827,11 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     CK(h->laststep.alloc(nS));
     CK(h->maxstep.alloc(nS));
     CK(h->stop.alloc(1));
+    CK(h->clk.alloc(6));
+    CK(h->clk_acc.alloc(4));
+    CK(h->steps_dev.alloc(1));
     CK(cudaMallocHost((void **)&h->h_n_active, sizeof(int)));
+    CK(cudaMallocHost((void **)&h->h_stop, sizeof(StopRule)));
     // measurement-function tables in canonical numbering
     {
         const int L = h->S.L;

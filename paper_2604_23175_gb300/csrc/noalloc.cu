@@ -1,15 +1,15 @@
 // Coordinator solve that allocates no device memory (mase_coordinator_noalloc).
 //
-// Some callers cannot call cudaMalloc when they need the coordinator: code
-// running while another thread captures a CUDA graph in global capture mode
-// (cudaMalloc is refused there), real-time loops that cannot afford the
-// device-wide synchronisation cudaMalloc implies, and hosts whose device
-// memory is owned by another allocator that forbids raw allocations.  This
-// entry point lets them run the coordinator step on condensed blocks they
-// already hold: its scratch (boundary-factor storage, the assembled copy used
-// by the refinement, small index tables and a status word per snapshot) lives
-// in one file-scope static device array of kScratchBytes, which every GPU
-// that loads the library keeps until the process exits.
+// Some callers cannot call cudaMalloc when they need the coordinator step:
+// a host program whose device memory belongs to another allocator (a
+// framework's caching pool, or a pool carved out once at start-up) that does
+// not allow raw allocations next to it, and latency-bound loops that must not
+// take the device-wide synchronisation cudaMalloc and cudaFree can imply.
+// This entry point lets them run the coordinator step on condensed blocks
+// they already hold: its scratch (boundary-factor storage, the assembled copy
+// used by the refinement, small index tables and a status word per snapshot)
+// lives in one file-scope static device array of kScratchBytes, which every
+// GPU that loads the library keeps until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -135,12 +135,29 @@ bool is_device(const void *p) {
 
 extern "C" {
 
-int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, const double *b_blocks,
-                             double *dx_gamma) {
+int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, int64_t n_S,
+                             const double *b_blocks, int64_t n_b, double *dx_gamma, int64_t n_dx) {
     using mase_internal::CoordView;
     CoordView v;
     if (!mase_internal::coord_view(h, v)) return fail(MASE_EINVAL, "null handle");
     if (!S_blocks || !b_blocks || !dx_gamma) return fail(MASE_EINVAL, "null argument");
+    {
+        // the element counts the handle implies, checked before any device work
+        long long need_S = 0, need_b = 0;
+        for (int k = 0; k < v.n_area; ++k) {
+            const long long nb = v.n_bnd[k];
+            need_S += nb * (nb + 1) / 2;
+            need_b += nb;
+        }
+        need_S *= v.n_snap;
+        need_b *= v.n_snap;
+        const long long need_dx = (long long)v.n_snap * v.B.n_gamma;
+        if (n_S != need_S || n_b != need_b || n_dx != need_dx)
+            return fail(MASE_EINVAL, "element counts (S_blocks " + std::to_string(n_S) + ", b_blocks " +
+                                         std::to_string(n_b) + ", dx_gamma " + std::to_string(n_dx) +
+                                         ") differ from the handle's (" + std::to_string(need_S) + ", " +
+                                         std::to_string(need_b) + ", " + std::to_string(need_dx) + ")");
+    }
     if (v.device < 0 || v.device >= kMaxDevices) return fail(MASE_EINVAL, "device ordinal out of range");
     if (cudaSetDevice(v.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice failed");
     if (!is_device(S_blocks) || !is_device(b_blocks) || !is_device(dx_gamma))

@@ -334,6 +334,9 @@ __global__ void k_colsum(const T *__restrict__ G, int B, int C, const long long 
     }
 }
 
+// AdamW constants of the warm-start training (also used by mase_adamw_check)
+constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+
 __global__ void k_adamw(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                         const float *__restrict__ g, bf16 *__restrict__ w16, long long n, float lr,
                         float b1, float b2, float eps, float wd, float bc1, float bc2) {
@@ -920,7 +923,7 @@ int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32
     DevBuf<int> idx;
     WK(idx.alloc((size_t)opt.batch * steps_per_epoch));
     double last_epoch_loss = 0;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float b1 = kAdamB1, b2 = kAdamB2, eps = kAdamEps;
     long long t = 0;
     for (int ep = 0; ep < opt.epochs; ++ep) {
         std::iota(perm.begin(), perm.end(), 0);
@@ -1185,6 +1188,38 @@ int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const f
             for (int i = 0; i < rin[ll]; ++i) grads[dst++] = G[n.w_off[ll] + (long long)o * din[ll] + i];
         for (int o = 0; o < rout[ll]; ++o) grads[dst++] = G[n.b_off[ll] + o];
     }
+    return MASE_OK;
+}
+
+// The optimiser step of the warm-start training on its own: the AdamW kernel
+// that training launches, run `steps` times with the caller's gradients and
+// learning rates, moments starting at zero (bias corrections as in training).
+int mase_adamw_check(int64_t n, int32_t steps, const float *lr, float weight_decay,
+                     const float *grads, float *w, float *m_out, float *v_out, uint16_t *w_bf16_out) {
+    if (n < 1 || steps < 1 || !lr || !grads || !w)
+        return fail(MASE_EINVAL, "mase_adamw_check needs n >= 1, steps >= 1, lr, grads and w");
+    DevBuf<float> dw, dm, dv, dg;
+    DevBuf<bf16> d16;
+    WK(dw.alloc(n));
+    WK(dm.alloc(n));
+    WK(dv.alloc(n));
+    WK(dg.alloc(n));
+    WK(d16.alloc(n));
+    WK(cudaMemcpy(dw.p, w, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+    WK(cudaMemset(dm.p, 0, (size_t)n * sizeof(float)));
+    WK(cudaMemset(dv.p, 0, (size_t)n * sizeof(float)));
+    for (int t = 1; t <= steps; ++t) {
+        WK(cudaMemcpy(dg.p, grads + (size_t)(t - 1) * n, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+        const float bc1 = 1.f - std::pow(kAdamB1, (float)t), bc2 = 1.f - std::pow(kAdamB2, (float)t);
+        k_adamw<<<grid_for(n), 256>>>(dw.p, dm.p, dv.p, dg.p, d16.p, n, lr[t - 1], kAdamB1, kAdamB2,
+                                      kAdamEps, weight_decay, bc1, bc2);
+        WK(cudaGetLastError());
+    }
+    WK(cudaDeviceSynchronize());
+    WK(cudaMemcpy(w, dw.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (m_out) WK(cudaMemcpy(m_out, dm.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (v_out) WK(cudaMemcpy(v_out, dv.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (w_bf16_out) WK(cudaMemcpy(w_bf16_out, d16.p, (size_t)n * sizeof(bf16), cudaMemcpyDeviceToHost));
     return MASE_OK;
 }
 

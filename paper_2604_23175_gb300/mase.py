@@ -44,12 +44,13 @@ class Measurements(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
-                ("stream", C.c_void_p), ("profile", C.c_int32), ("inner_iters", C.c_int32)]
+                ("stream", C.c_void_p), ("profile", C.c_int32), ("wait_polls", C.c_int32),
+                ("inner_iters", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", _i32p), ("status", _i32p), ("J", _f64p), ("max_step", _f64p),
-                ("stage_ms", C.c_double * 4), ("total_launches", C.c_int32),
+                ("stage_ms", C.c_double * 7), ("solve_ms", C.c_double), ("total_launches", C.c_int32),
                 ("steps", C.c_int32)]
 
 
@@ -68,7 +69,8 @@ class Info(C.Structure):
                 ("smem_bytes_max", C.c_int32), ("areas_in_smem", C.c_int32),
                 ("n_supernodes", C.c_int64), ("n_units", C.c_int64), ("max_levels", C.c_int32),
                 ("max_area_store", C.c_int32), ("boundary_store", C.c_int32),
-                ("boundary_levels", C.c_int32)]
+                ("boundary_levels", C.c_int32), ("coord_S_elems", C.c_int64),
+                ("coord_b_elems", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,13 +109,18 @@ def load() -> C.CDLL:
         "mase_analyze": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.POINTER(Info)]),
         "mase_selfcheck": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.c_uint64, _f64p]),
         "mase_analyze_error": (C.c_char_p, []),
-        "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                               C.c_void_p, C.c_int64]),
         "mase_warmstart_default_options": (None, [C.POINTER(WarmstartOptions)]),
         "mase_warmstart_train": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int32,
                                            C.POINTER(WarmstartOptions), C.POINTER(C.c_double)]),
         "mase_warmstart_predict": (C.c_int, [H, C.c_void_p]),
         "mase_warmstart_save": (C.c_int, [H, C.c_char_p]),
         "mase_warmstart_load": (C.c_int, [H, C.c_char_p]),
+        "mase_adamw_check": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(C.c_float), C.c_float,
+                                       C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_uint16)]),
         "mase_mlp_check": (C.c_int, [_i32p, C.c_int32, C.c_int32, C.POINTER(C.c_float),
                                      C.POINTER(C.c_float), C.POINTER(C.c_float),
                                      C.POINTER(C.c_float), C.POINTER(C.c_float)]),
@@ -197,6 +204,29 @@ def default_options() -> Options:
     return o
 
 
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
+
+
+def noalloc_sizes(info: dict, n_snap: int) -> tuple:
+    """Element counts (S_blocks, b_blocks, dx_gamma) the no-alloc coordinator
+    step expects for a handle with this structure and batch size."""
+    return (n_snap * int(info["coord_S_elems"]), n_snap * int(info["coord_b_elems"]),
+            n_snap * int(info["n_gamma"]))
+
+
+def check_noalloc_args(need: tuple, S_blocks, b_blocks, dx_gamma) -> None:
+    """Rejects (ValueError) tensors whose dtype is not float64 or whose size
+    differs from ``need`` before anything is launched."""
+    for name, t, n in (("S_blocks", S_blocks, need[0]), ("b_blocks", b_blocks, need[1]),
+                       ("dx_gamma", dx_gamma, need[2])):
+        dt = str(getattr(t, "dtype", ""))
+        if dt not in ("torch.float64", "float64"):
+            raise ValueError(f"{name} must be float64, got {dt or type(t).__name__}")
+        if _numel(t) != n:
+            raise ValueError(f"{name} has {_numel(t)} elements, the handle needs {n}")
+
+
 @dataclass
 class SolveResult:
     rc: int
@@ -206,7 +236,8 @@ class SolveResult:
     max_step: np.ndarray
     launches: int
     steps: int
-    stage_ms: tuple
+    stage_ms: tuple     # area, coordinator, back, bookkeeping, learned start, start/finish, loop gaps
+    solve_ms: float
 
 
 class Estimator:
@@ -214,7 +245,7 @@ class Estimator:
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
                  schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
-                 profile=False, inner_iters=0):
+                 profile=False, wait_polls=0, inner_iters=0):
         self.lib = load()
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -223,6 +254,7 @@ class Estimator:
         opt.refine, opt.threads, opt.device = refine, threads, device
         opt.stream = C.c_void_p(stream) if stream else None
         opt.profile = int(bool(profile))
+        opt.wait_polls = int(wait_polls)
         opt.inner_iters = int(inner_iters)
         meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
         h = C.c_void_p()
@@ -270,7 +302,7 @@ class Estimator:
         if check and rc < 0:
             raise MaseError(rc, _last_error())
         return SolveResult(rc, iters, status, J, ms, int(st.total_launches), int(st.steps),
-                           tuple(st.stage_ms))
+                           tuple(st.stage_ms), float(st.solve_ms))
 
     def measure(self, x, z_out, n_snap=None):
         n = self.n_snap if n_snap is None else n_snap
@@ -280,8 +312,13 @@ class Estimator:
 
     def coordinator_noalloc(self, S_blocks, b_blocks, dx_gamma):
         """Coordinator step on caller-held condensed blocks, without device
-        allocation (device tensors in, device tensor out)."""
-        rc = self.lib.mase_coordinator_noalloc(self.h, _ptr(S_blocks), _ptr(b_blocks), _ptr(dx_gamma))
+        allocation (FP64 device tensors in, FP64 device tensor out).  Sizes and
+        dtypes are checked here first; the C entry point checks the counts
+        again."""
+        need = noalloc_sizes(self.info(), self.n_snap)
+        check_noalloc_args(need, S_blocks, b_blocks, dx_gamma)
+        rc = self.lib.mase_coordinator_noalloc(self.h, _ptr(S_blocks), _numel(S_blocks), _ptr(b_blocks),
+                                               _numel(b_blocks), _ptr(dx_gamma), _numel(dx_gamma))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
 
@@ -338,3 +375,25 @@ def mlp_check(dims, params, X, T):
     if rc != MASE_OK:
         raise MaseError(rc, _last_error())
     return loss.value, g
+
+
+def adamw_check(w, grads, lr, weight_decay):
+    """Runs the library's AdamW kernel len(lr) times on FP32 parameters w with
+    the given gradients [steps, n]; returns (w, m, v, w_bf16_bits)."""
+    lib = load()
+    wa = np.array(w, dtype=np.float32, copy=True)
+    ga = np.ascontiguousarray(grads, dtype=np.float32)
+    la = np.ascontiguousarray(lr, dtype=np.float32)
+    n, steps = wa.size, la.size
+    if ga.shape != (steps, n):
+        raise ValueError("grads must be [steps, n]")
+    m = np.zeros(n, dtype=np.float32)
+    v = np.zeros(n, dtype=np.float32)
+    w16 = np.zeros(n, dtype=np.uint16)
+    fp = C.POINTER(C.c_float)
+    rc = lib.mase_adamw_check(n, steps, la.ctypes.data_as(fp), float(weight_decay), ga.ctypes.data_as(fp),
+                              wa.ctypes.data_as(fp), m.ctypes.data_as(fp), v.ctypes.data_as(fp),
+                              w16.ctypes.data_as(C.POINTER(C.c_uint16)))
+    if rc != MASE_OK:
+        raise MaseError(rc, _last_error())
+    return wa, m, v, w16

@@ -346,3 +346,182 @@ def family_mask(grid: Grid, family: str, n_snap: int = 1) -> np.ndarray:
     row = np.ones(grid.n_meas, dtype=np.uint8)
     row[o:o + c] = 0
     return np.repeat(row[None, :], n_snap, axis=0)
+
+
+# ---------------------------------------------------------------------------
+# partitioning one fixed network into K areas (the paper's K-sweep, Sec. 5.3,
+# re-partitions one network; its "tree partitions" are not specified)
+# ---------------------------------------------------------------------------
+def _adjacency(n: int, f: np.ndarray, t: np.ndarray) -> list[list[int]]:
+    nb = [set() for _ in range(n)]
+    for a, b in zip(f.tolist(), t.tolist()):
+        nb[a].add(b)
+        nb[b].add(a)
+    return [sorted(s) for s in nb]
+
+
+def _bfs_far(start: int, member: set, adj) -> tuple[int, list[int]]:
+    """BFS inside ``member`` from ``start``: (last node reached, visit order)."""
+    seen = {start}
+    order = [start]
+    q = deque([start])
+    while q:
+        a = q.popleft()
+        for c in adj[a]:
+            if c in member and c not in seen:
+                seen.add(c)
+                order.append(c)
+                q.append(c)
+    return order[-1], order
+
+
+def _fiedler(nodes: list[int], adj) -> np.ndarray:
+    """Second eigenvector of the graph Laplacian of the subgraph on ``nodes``
+    (shift-invert Lanczos near 0)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    loc = {v: i for i, v in enumerate(nodes)}
+    r, c = [], []
+    for v in nodes:
+        for u in adj[v]:
+            if u in loc:
+                r.append(loc[v])
+                c.append(loc[u])
+    n = len(nodes)
+    A = sp.csr_matrix((np.ones(len(r)), (r, c)), shape=(n, n))
+    Lap = sp.diags(np.asarray(A.sum(axis=1)).ravel()) - A
+    if n < 64:
+        w, V = np.linalg.eigh(Lap.toarray())
+        return V[:, 1]
+    w, V = spla.eigsh(Lap.tocsc(), k=2, sigma=-1e-3, which="LM",
+                      v0=np.linspace(1.0, 2.0, n))
+    return V[:, np.argsort(w)[1]]
+
+
+def _bisect(nodes: list[int], target: int, adj, rng, tol: int) -> tuple[list[int], list[int]]:
+    """Split ``nodes`` along the Fiedler vector of their subgraph: the sweep
+    cut with the fewest cut branches among first-part sizes within ``tol`` of
+    ``target``, then greedy boundary moves that cut fewer branches while the
+    first part stays within the same window."""
+    member = set(nodes)
+    f = _fiedler(nodes, adj)
+    order = [nodes[i] for i in np.argsort(f, kind="stable")]
+    pos = {v: i for i, v in enumerate(order)}
+    # cut(prefix of length p) updated incrementally along the sweep
+    cut = 0
+    best_p, best_cut = target, None
+    for p_, v in enumerate(order, start=1):
+        for u in adj[v]:
+            if u in member:
+                cut += 1 if pos[u] >= p_ else -1
+        if target - tol <= p_ <= target + tol and (best_cut is None or cut < best_cut):
+            best_p, best_cut = p_, cut
+    side = {v: (0 if pos[v] < best_p else 1) for v in nodes}
+    size0 = best_p
+    for _ in range(12):
+        moved = 0
+        cand = [v for v in nodes if any(c in member and side[c] != side[v] for c in adj[v])]
+        rng.shuffle(cand)
+        for v in cand:
+            sv = side[v]
+            ext = sum(1 for c in adj[v] if c in member and side[c] != sv)
+            inn = sum(1 for c in adj[v] if c in member and side[c] == sv)
+            if ext <= inn:
+                continue
+            new0 = size0 - 1 if sv == 0 else size0 + 1
+            if abs(new0 - target) > tol:
+                continue
+            side[v] = 1 - sv
+            size0 = new0
+            moved += 1
+        if not moved:
+            break
+    a = [v for v in nodes if side[v] == 0]
+    b = [v for v in nodes if side[v] == 1]
+    return a, b
+
+
+def partition_network(grid: Grid, n_area: int, seed: int = 0, imbalance: float = 0.25) -> Grid:
+    """The same network split into ``n_area`` connected areas: recursive
+    spectral bisection (sweep cut of the Fiedler vector with the fewest cut
+    branches among splits within ``imbalance`` of proportional sizes, then
+    greedy boundary moves that cut fewer branches), a K-way pass of the same
+    greedy moves, and reassignment of any disconnected piece of an area to
+    the neighbouring area it shares most branches with.  Deterministic for a
+    seed.  Returns a Grid with the same branches and the new partition."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = grid.n_bus
+    adj = _adjacency(N, grid.from_bus, grid.to_bus)
+    area = np.empty(N, dtype=np.int64)
+    stack = [(list(range(N)), n_area, 0)]
+    while stack:
+        nodes, k, a0 = stack.pop()
+        if k == 1:
+            area[nodes] = a0
+            continue
+        k1 = k // 2
+        target = int(round(len(nodes) * k1 / k))
+        tol = max(1, int(imbalance * len(nodes) * k1 / k))
+        left, right = _bisect(nodes, target, adj, rng, tol)
+        stack.append((left, k1, a0))
+        stack.append((right, k - k1, a0 + k1))
+    # K-way greedy refinement with a size band around N / K
+    sizes = np.bincount(area, minlength=n_area)
+    lo, hi = (1 - 2 * imbalance) * N / n_area, (1 + 2 * imbalance) * N / n_area
+    for _ in range(8):
+        moved = 0
+        for v in rng.permutation(N).tolist():
+            av = area[v]
+            cnt = {}
+            for c in adj[v]:
+                cnt[area[c]] = cnt.get(area[c], 0) + 1
+            own = cnt.get(av, 0)
+            best, gain = av, 0
+            for a, c in cnt.items():
+                if a != av and c - own > gain and sizes[a] + 1 <= hi and sizes[av] - 1 >= lo:
+                    best, gain = a, c - own
+            if best != av:
+                area[v] = best
+                sizes[av] -= 1
+                sizes[best] += 1
+                moved += 1
+        if not moved:
+            break
+    # connectivity: pieces other than an area's largest join a neighbouring area
+    for _ in range(N):
+        changed = False
+        for k in range(n_area):
+            members = set(np.nonzero(area == k)[0].tolist())
+            comps = []
+            left = set(members)
+            while left:
+                s = min(left)
+                _, order = _bfs_far(s, left, adj)
+                comps.append(order)
+                left.difference_update(order)
+            if len(comps) <= 1:
+                continue
+            comps.sort(key=len, reverse=True)
+            for comp in comps[1:]:
+                cnt = {}
+                cs = set(comp)
+                for v in comp:
+                    for c in adj[v]:
+                        if c not in cs:
+                            cnt[area[c]] = cnt.get(area[c], 0) + 1
+                cnt.pop(k, None)
+                if cnt:
+                    area[comp] = max(sorted(cnt), key=lambda a: cnt[a])
+                    changed = True
+        if not changed:
+            break
+    if len(np.unique(area)) != n_area:
+        raise RuntimeError("partition lost an area")
+    return Grid(N, grid.from_bus, grid.to_bus, grid.r, grid.x, grid.b_charge, area.astype(np.int32),
+                n_area, grid.slack, f"{grid.name}_p{n_area}",
+                meta={"partitioned_from": grid.name, "seed": seed})
+
+
+def cut_branches(grid: Grid) -> int:
+    """Number of branches whose terminals lie in different areas."""
+    return int(np.sum(grid.area_of_bus[grid.from_bus] != grid.area_of_bus[grid.to_bus]))

@@ -4,6 +4,8 @@ Measurements are formed with the oracle's measurement functions, so no test
 input or expected value ever comes from the CUDA path."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from oracle import wls
@@ -49,3 +51,27 @@ def tiny_grid(n_bus=10, n_area=3, seed=7, slack_on_boundary=False):
     L = len(edges)
     return synth.Grid(n_bus, f, t, rng.uniform(0.002, 0.02, L), rng.uniform(0.02, 0.2, L),
                       rng.uniform(0.0, 0.05, L), area, n_area, 0, "tiny")
+
+
+def _gn_one(args):
+    net, z, w, x0, tol, max_iter, keep_steps = args
+    N = net.n_bus
+    v0 = (None, None) if x0 is None else (x0[:N], x0[N:])
+    return wls.gauss_newton(net, z, w, Vm0=v0[0], Va0=v0[1], tol=tol, max_iter=max_iter,
+                            keep_steps=keep_steps)
+
+
+def oracle_gn_many(net, z, w, x0=None, tol=1e-8, max_iter=30, keep_steps=False):
+    """The oracle's centralised Gauss-Newton for every snapshot of z [S, m],
+    in worker processes started with spawn (safe after CUDA is initialised).
+    w is one weight vector or one per snapshot."""
+    import multiprocessing as mp
+    S = z.shape[0]
+    ws = [w if w.ndim == 1 else w[s] for s in range(S)] if hasattr(w, "ndim") else [w] * S
+    args = [(net, z[s], ws[s], None if x0 is None else x0[s], tol, max_iter, keep_steps)
+            for s in range(S)]
+    procs = max(1, min(S, os.cpu_count() or 1, 16))
+    if procs == 1:
+        return [_gn_one(a) for a in args]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_gn_one, args)

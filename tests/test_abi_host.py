@@ -100,3 +100,27 @@ def test_invalid_inputs_rejected_on_host(mase):
     bad3.from_bus[0] = g.n_bus
     with pytest.raises(mase.MaseError):
         mase.analyze(bad3)
+
+
+def test_noalloc_argument_checks_on_host(mase):
+    """The binding's size and dtype checks of the no-alloc coordinator step,
+    with sizes from the host-only analysis (no GPU): short or FP32 buffers are
+    refused before any call into the library."""
+    g = synth.make_grid("grid2869_k16")
+    info = mase.analyze(g)
+    part = wls.partition(net_of(g), g.area_of_bus, g.n_area)
+    nbs = [len(c) for c in part.boundary_cols]
+    assert info["coord_S_elems"] == sum(n * (n + 1) // 2 for n in nbs)
+    assert info["coord_b_elems"] == sum(nbs)
+    need = mase.noalloc_sizes(info, 3)
+    ok = [np.zeros(n) for n in need]
+    mase.check_noalloc_args(need, *ok)
+    for i in range(3):
+        short = list(ok)
+        short[i] = np.zeros(need[i] - 1)
+        with pytest.raises(ValueError):
+            mase.check_noalloc_args(need, *short)
+        f32 = list(ok)
+        f32[i] = np.zeros(need[i], dtype=np.float32)
+        with pytest.raises(ValueError):
+            mase.check_noalloc_args(need, *f32)

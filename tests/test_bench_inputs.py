@@ -1,6 +1,7 @@
 """The benchmark's workload variants (CPU only): the sweep over the number of
-areas draws the headline grid itself at 32 areas, and a dropped family masks
-exactly that family's rows."""
+areas re-partitions the headline network itself (same buses and branches,
+only the partition changes), the default is the headline grid, and a dropped
+family masks exactly that family's rows."""
 import argparse
 import os
 import sys
@@ -19,17 +20,20 @@ def _inputs(areas, snapshots=2):
                                                     snapshots=snapshots))
 
 
-def test_area_sweep_at_32_is_the_benchmark_grid():
-    g, *_ = _inputs(32)
+def test_default_is_the_benchmark_grid():
+    g, *_ = _inputs(0)
     h = synth.make_grid(bench.WORKLOAD)
     for f in ("from_bus", "to_bus", "r", "x", "b_charge", "area_of_bus"):
         np.testing.assert_array_equal(getattr(g, f), getattr(h, f))
 
 
-def test_area_sweep_keeps_the_network_size():
-    for K in (16, 64):
+def test_area_sweep_repartitions_the_same_network():
+    h = synth.make_grid(bench.WORKLOAD)
+    for K in (16, 48):
         g, *_ = _inputs(K)
         assert (g.n_bus, g.n_branch, g.n_area) == (9241, 16049, K)
+        for f in ("from_bus", "to_bus", "r", "x", "b_charge"):
+            np.testing.assert_array_equal(getattr(g, f), getattr(h, f))
         assert np.bincount(g.area_of_bus, minlength=K).min() > 0
 
 
@@ -39,3 +43,13 @@ def test_family_mask_drops_one_family():
     m = synth.family_mask(g, "Qt", 3)
     assert m.shape == (3, g.n_meas)
     assert np.all(m[:, 3 * N + 3 * L:] == 0) and np.all(m[:, :3 * N + 3 * L] == 1)
+
+
+def test_oracle_baseline_children_on_a_small_grid():
+    """The CPU baseline's worker processes (centralised and multi-area
+    oracle) solve their snapshots and agree with each other."""
+    argv = ["--workload", "grid300_k4", "--snapshots", "4"]
+    wall, outs, x = bench.oracle_run(argv, [[0], [1]])
+    assert x.shape == (2, 600) and wall > 0 and all(o["iters"][0] >= 2 for o in outs)
+    wall2, outs2, x2 = bench.oracle_run(argv, [[0, 1]], multi=True)
+    assert np.max(np.abs(x - x2)) < 1e-9

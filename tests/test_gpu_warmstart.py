@@ -57,6 +57,56 @@ def test_training_kernels_match_oracle_gradients(mase, dims, batch):
         assert got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref)) > 0.999
 
 
+def _bf16_bits_rne(a32):
+    """Round-to-nearest-even of FP32 values to BF16, as raw 16-bit patterns."""
+    u = np.asarray(a32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)
+
+
+def test_adamw_kernel_matches_oracle(mase):
+    """The training's AdamW kernel (FP32) against the FP64 oracle update over
+    20 steps with a cosine learning-rate schedule and weight decay, on
+    parameters and gradients spanning several magnitudes (zero and tiny
+    gradients exercise pure decay and eps).  The oracle gets the kernel's
+    constants as the FP32 numbers they are.  Bar, with u = 2^-24: a few
+    roundings per operation, plus the FP32 bias corrections 1 - beta^t, whose
+    rounding is amplified by beta^t / (1 - beta^t)."""
+    rng = np.random.default_rng(11)
+    n, steps = 4099, 20
+    f32 = lambda x: float(np.float32(x))
+    b1, b2, eps, wd = f32(0.9), f32(0.999), f32(1e-8), f32(1e-2)
+    w0 = (rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 1, n)).astype(np.float32)
+    grads = (rng.standard_normal((steps, n)) * 10.0 ** rng.uniform(-9, 1, (1, n))).astype(np.float32)
+    grads[:, :7] = 0.0
+    lr = (1e-3 * (0.05 + 0.95 * 0.5 * (1 + np.cos(np.pi * np.arange(steps) / (steps - 1))))).astype(np.float32)
+    w, m, v, w16 = mase.adamw_check(w0, grads, lr, wd)
+    u = 2.0 ** -24
+    wr = w0.astype(np.float64)
+    mr = np.zeros(n)
+    vr = np.zeros(n)
+    bw = np.zeros(n)      # error bounds, accumulated along the oracle's trajectory
+    bm = np.zeros(n)
+    bv = np.zeros(n)
+    for t in range(1, steps + 1):
+        g = grads[t - 1].astype(np.float64)
+        lt = float(lr[t - 1])
+        bm = b1 * bm + 3 * u * (b1 * np.abs(mr) + (1 - b1) * np.abs(g))
+        bv = b2 * bv + 3 * u * (b2 * vr + (1 - b2) * g * g)
+        w_prev = wr.copy()
+        mr, vr = omlp.adamw_step(wr, g, mr, vr, t, lt, beta1=b1, beta2=b2, eps=eps, wd=wd)
+        step = np.abs(w_prev * (1 - lt * wd) - wr)
+        amp = u * (b1 ** t / (1 - b1 ** t) + 0.5 * b2 ** t / (1 - b2 ** t))
+        rel_m = bm / np.maximum(np.abs(mr), 1e-300)
+        bw = bw + 3 * u * np.abs(w_prev) + step * (8 * u + amp + np.minimum(rel_m, 1.0)) \
+            + lt * bm / (1 - b1 ** t) / (np.sqrt(vr / (1 - b2 ** t)) + eps) * (rel_m > 1.0)
+    assert np.all(np.abs(w - wr) <= 2 * bw + 1e-30), np.max(np.abs(w - wr) / (bw + 1e-30))
+    assert np.all(np.abs(m - mr) <= 2 * bm + 1e-38)
+    assert np.all(np.abs(v - vr) <= 2 * bv + 1e-38)
+    # the BF16 copy the networks compute with is the FP32 master rounded to nearest even
+    assert np.array_equal(w16, _bf16_bits_rne(w))
+
+
 def _batch(mase, est, g, seed, S, walk=None):
     import torch
     Vm, Va = synth.make_states(g, S, seed, walk_len=walk)

@@ -1,12 +1,12 @@
 """The allocation-free coordinator entry point (mase_coordinator_noalloc).
 
 It serves callers that cannot call cudaMalloc when they need the coordinator
-step (for example while a CUDA graph is being captured in global mode, or in
-a real-time loop).  The test feeds it the condensed per-area blocks
-(S_b, b_hat_b) of a state x0, computed by the CPU oracle, and compares its
-boundary step with the step that the existing entry point mase_solve takes
-from x0 (one Gauss-Newton step), on two calls in a row.  This file is named to
-be collected last.
+step: programs whose device memory belongs to another allocator, and
+latency-bound loops that must not take the synchronisation an allocation can
+imply.  The test feeds it the condensed per-area blocks (S_b, b_hat_b) of a
+state x0, computed by the CPU oracle, and compares its boundary step with the
+step that the existing entry point mase_solve takes from x0 (one Gauss-Newton
+step), on two calls in a row.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -119,9 +119,37 @@ def test_coordinator_noalloc_rejects_oversized_request(mase):
     sig = synth.sigma_vector(g.n_bus, g.n_branch)
     # 64 snapshots of the FP64 boundary system need more than the static maximum
     est = mase.Estimator(g, sig, 64, z=None, precision=mase.FP64, schedule=mase.BATCHED)
-    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    nS, nb, ndx = mase.noalloc_sizes(est.info(), 64)
+    Sd = torch.zeros(nS, dtype=torch.float64, device="cuda")
+    bd = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    dx = torch.zeros(ndx, dtype=torch.float64, device="cuda")
     with pytest.raises(mase.MaseError) as e:
-        est.coordinator_noalloc(dummy, dummy, dummy)
+        est.coordinator_noalloc(Sd, bd, dx)
     assert e.value.code == mase.MASE_EINVAL
     assert "static maximum" in str(e.value)
+    est.close()
+
+
+def test_coordinator_noalloc_checks_element_counts(mase):
+    """Short buffers are refused by the C entry point itself (before any
+    device work) and by the binding (with FP32 tensors too)."""
+    import ctypes
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    S = 2
+    net, Vm, Va, z, sig = problem(g, S, 5300)
+    est = mase.Estimator(g, sig, S, z=z, precision=mase.FP64, schedule=mase.BATCHED)
+    nS, nb, ndx = mase.noalloc_sizes(est.info(), S)
+    Sd = torch.zeros(nS, dtype=torch.float64, device="cuda")
+    bd = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    dx = torch.zeros(ndx, dtype=torch.float64, device="cuda")
+    lib = mase.load()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    for counts in ((nS - 1, nb, ndx), (nS, nb - 1, ndx), (nS, nb, ndx + 1)):
+        rc = lib.mase_coordinator_noalloc(est.h, p(Sd), counts[0], p(bd), counts[1], p(dx), counts[2])
+        assert rc == mase.MASE_EINVAL
+    with pytest.raises(ValueError):
+        est.coordinator_noalloc(Sd[:-1], bd, dx)
+    with pytest.raises(ValueError):
+        est.coordinator_noalloc(Sd.float(), bd, dx)
     est.close()
