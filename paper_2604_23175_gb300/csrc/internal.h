@@ -110,7 +110,11 @@ struct mase_handle {
     DevBuf<int> active, err, iters, status, n_active;
     DevBuf<unsigned long long> maxstep;
     int *h_n_active = nullptr;   // pinned
-    size_t smem_local = 0, smem_back = 0, smem_bnd = 0;
+    size_t smem_local = 0, smem_back = 0, smem_bnd = 0, smem_obj = 0;
+    // areas whose vectors live in global scratch (one area holding a large network)
+    int vec_global = 0;
+    long long vscratch_bytes = 0;
+    DevBuf<unsigned char> vscratch;
     // coordinator on 2-block clusters (the whole boundary factor on chip)
     int bnd_cluster = 0;
     size_t smem_bnd_cl = 0;

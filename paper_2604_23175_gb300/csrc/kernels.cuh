@@ -48,6 +48,13 @@ struct AreaDev {
     int off_g, off_y, off_bus, off_end, off_inj, off_self, off_st;   // dynamic smem byte offsets
     int smem_bytes;
     int back_smem_bytes;    // dynamic shared memory of the back-substitution (rhs)
+    int obj_off_end;        // objective kernel: byte offset of the end flows
+    int obj_smem_bytes;     // objective kernel: dynamic shared memory
+    // areas whose vectors exceed shared memory (e.g. one area holding the
+    // whole network) keep them in global scratch, vec_stride bytes per snapshot
+    int vec_global;
+    int vec_stride;
+    long long vec_base;
     long long fac_base;     // element offset of (area, snapshot 0) in the factor buffer
     int fac_stride;         // elements per snapshot (= store_total)
     long long c_base;       // interior forward-solved rhs, stride n_int
@@ -678,12 +685,12 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y
 // ---------------------------------------------------------------------------
 // local kernel: evaluation + fused accumulation + Schur condensation
 // ---------------------------------------------------------------------------
-enum { MODE_FULL = 0, MODE_OBJECTIVE = 1 };
-
-template <class RG, class RS>
+// VG: some areas keep their vectors in global scratch (vscratch); compiled
+// separately so that the usual all-on-chip kernel addresses shared memory only.
+template <class RG, class RS, bool VG>
 __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas, Tables T, State X,
                                                const int2 *__restrict__ inst, int area_only,
-                                               int mode, RG *fac, RS *cvec, double *bh) {
+                                               RG *fac, RS *cvec, double *bh, unsigned char *vscratch) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ int s_err;
@@ -696,20 +703,25 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         k = ks.x;
         s = ks.y;
     }
-    if (mode == MODE_FULL && !X.active[s]) return;
+    if (!X.active[s]) return;
     clk_begin(X.clk);
     const AreaDev A = areas[k];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nv = A.F.n_int + A.F.n_bnd;
-    double *g = (double *)(smem + A.off_g);
-    RS *y = (RS *)(smem + A.off_y);
-    double *bV = (double *)(smem + A.off_bus);
+    const bool vglob = VG && A.vec_global;
+    unsigned char *vb = vglob ? vscratch + A.vec_base + (long long)s * A.vec_stride : smem;
+    double *g = (double *)(vb + A.off_g);
+    RS *y = (RS *)(vb + A.off_y);
+    double *bV = (double *)(vb + A.off_bus);
     double *bC = bV + A.nb_loc;
     double *bS = bC + A.nb_loc;
-    unsigned char *endbuf = smem + A.off_end;
-    double2 *inj = (double2 *)(smem + A.off_inj);
-    RG *self = (RG *)(smem + A.off_self);
-    RG *st = A.in_smem ? (RG *)(smem + A.off_st) : fac + A.fac_base + (long long)s * A.fac_stride;
+    unsigned char *endbuf = vb + A.off_end;
+    double2 *inj = (double2 *)(vb + A.off_inj);
+    RG *self = (RG *)(vb + A.off_self);
+    RG *st = A.in_smem ? (RG *)(vb + A.off_st) : fac + A.fac_base + (long long)s * A.fac_stride;
+    // dataflow counters: the bus-value region once evaluation is done, or the
+    // block's own shared memory when the vectors are global
+    int *ctr = vglob ? (int *)smem : (int *)(vb + A.off_bus);
     const int endstride = (4 * sizeof(RG) > 16) ? 4 * (int)sizeof(RG) : 16;
 
     const long long zb = (long long)s * X.M + A.zrow_base;
@@ -731,11 +743,9 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         bC[q] = cs;
         bS[q] = sn;
     }
-    if (mode == MODE_FULL) {
-        for (int i = tid; i < nv; i += nt) g[i] = 0.0;
-        for (int i = tid; i < A.F.store_total; i += nt) st[i] = RG(0);
-        for (int i = tid; i < 4 * n_own; i += nt) self[i] = RG(0);
-    }
+    for (int i = tid; i < nv; i += nt) g[i] = 0.0;
+    for (int i = tid; i < A.F.store_total; i += nt) st[i] = RG(0);
+    for (int i = tid; i < 4 * n_own; i += nt) self[i] = RG(0);
     __syncthreads();
     // ---- E1: flows at every owned branch end (FP64)
     for (int e = tid; e < n_ends; e += nt) {
@@ -765,10 +775,8 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         const double rp = z[rP + o] - Pi, rq = z[rQ + o] - Qi;
         Jloc += wp * rp * rp + wq * rq * rq;
         inj[o] = make_double2(wp * rp, wq * rq);
-        if (mode == MODE_FULL) {
-            atomicAdd(g + T.qvarV[A.bus_base + q], wv * rv);
-            atomicAdd(st + T.own_gvv[A.own_base + o], RG(wv));
-        }
+        atomicAdd(g + T.qvarV[A.bus_base + q], wv * rv);
+        atomicAdd(st + T.own_gvv[A.own_base + o], RG(wv));
     }
     __syncthreads();
     // ---- E3: flow rows; gradient of flow and injection rows; flow-row gain terms
@@ -779,7 +787,6 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         const double wPe = wt(rPe + e), wQe = wt(rQe + e);
         const double rPf = z[rPe + e] - pq.x, rQf = z[rQe + e] - pq.y;
         Jloc += wPe * rPf * rPf + wQe * rQf * rQf;
-        if (mode != MODE_FULL) continue;
         const double Vi = bV[qi], Vj = bV[qj];
         const double g_ = T.end_g[ee], b_ = T.end_b[ee], bh_ = T.end_bh[ee];
         const double2 tr = end_trig(bC[qi], bS[qi], bC[qj], bS[qj], g_, b_);
@@ -831,11 +838,6 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         nb[2] = hQ[2];
         nb[3] = hQ[3];
     }
-    if (mode != MODE_FULL) {
-        const double Js = block_sum(Jloc, red);
-        if (tid == 0) atomicAdd(X.J + s, Js);
-        return;
-    }
     __syncthreads();
     // ---- E4: injection-row gain terms, one item per pair of buses in the row
     for (int it = tid; it < A.n_items; it += nt) {
@@ -882,8 +884,7 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
     for (int i = tid; i < nv; i += nt) y[i] = RS(g[i]);
     __syncthreads();
     // ---- Schur-mode factorisation (Sec. 4.3): leaves S_b and b_hat in the trailing block
-    // the bus-value region is free from here on: task counters
-    factor_tasks<RG, RS>(A.F, T, FlatStore<RG>{st}, y, (int *)(smem + A.off_bus), &s_err);
+    factor_tasks<RG, RS>(A.F, T, FlatStore<RG>{st}, y, ctr, &s_err);
     // ---- outputs
     if (A.in_smem) {
         RG *dst = fac + A.fac_base + (long long)s * A.fac_stride;
@@ -1224,6 +1225,69 @@ __global__ void k_state_out(double *__restrict__ x, const double *xV, const doub
                             const int *__restrict__ bus_of_ibus, int N, int S);
 
 #ifndef MASE_SHARED_TEMPLATES_ONLY
+// ---------------------------------------------------------------------------
+// objective J = r^T W r at the current states (Eq. wls), per snapshot
+// ---------------------------------------------------------------------------
+// One block per (area, snapshot) evaluates the area's rows: voltage rows,
+// flow rows at every owned branch end and injection rows as sums of those
+// flows.  Shared memory holds only the bus values and the end flows
+// (AreaDev::obj_smem_bytes), so several blocks share an SM.
+template <bool VG>
+__global__ void __launch_bounds__(256) k_objective(const AreaDev *__restrict__ areas, Tables T, State X,
+                                                   const int2 *__restrict__ inst, unsigned char *vscratch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    const int2 ks = inst[blockIdx.x];
+    const int k = ks.x, s = ks.y;
+    const AreaDev A = areas[k];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    unsigned char *vb = (VG && A.vec_global) ? vscratch + A.vec_base + (long long)s * A.vec_stride : smem;
+    double *bV = (double *)vb;
+    double *bC = bV + A.nb_loc;
+    double *bS = bC + A.nb_loc;
+    double2 *pq = (double2 *)(vb + A.obj_off_end);
+    const long long zb = (long long)s * X.M + A.zrow_base;
+    const double *z = X.z + zb;
+    const double *Wr = X.W + A.zrow_base;
+    const uint8_t *mk = X.mask ? X.mask + zb : nullptr;
+    auto wt = [&](int r) { return mk ? (mk[r] ? Wr[r] : 0.0) : Wr[r]; };
+    const int n_own = A.n_own, n_ends = A.n_ends;
+    const int rP = n_own, rQ = 2 * n_own, rPe = 3 * n_own, rQe = 3 * n_own + n_ends;
+    for (int q = tid; q < A.nb_loc; q += nt) {
+        const int ib = T.locbus[A.bus_base + q];
+        double sn, cs;
+        sincos(X.xT[(long long)s * X.N + ib], &sn, &cs);
+        bV[q] = X.xV[(long long)s * X.N + ib];
+        bC[q] = cs;
+        bS[q] = sn;
+    }
+    __syncthreads();
+    double Jloc = 0.0;
+    for (int e = tid; e < n_ends; e += nt) {
+        const int ee = A.end_base + e;
+        const int qi = T.end_qi[ee], qj = T.end_qj[ee];
+        const EndFlow f = end_flow(bV[qi], bV[qj], bC[qi], bS[qi], bC[qj], bS[qj], T.end_g[ee],
+                                   T.end_b[ee], T.end_bh[ee]);
+        pq[e] = make_double2(f.P, f.Q);
+        const double rPf = z[rPe + e] - f.P, rQf = z[rQe + e] - f.Q;
+        Jloc += wt(rPe + e) * rPf * rPf + wt(rQe + e) * rQf * rQf;
+    }
+    __syncthreads();
+    for (int o = tid; o < n_own; o += nt) {
+        const int q = T.own_q[A.own_base + o];
+        const double rv = z[o] - bV[q];
+        double Pi = 0.0, Qi = 0.0;
+        for (int e = T.own_ebeg[A.own1_base + o]; e < T.own_ebeg[A.own1_base + o + 1]; ++e) {
+            Pi += pq[e].x;
+            Qi += pq[e].y;
+        }
+        const double rp = z[rP + o] - Pi, rq = z[rQ + o] - Qi;
+        Jloc += wt(o) * rv * rv + wt(rP + o) * rp * rp + wt(rQ + o) * rq * rq;
+    }
+    const double Js = block_sum(Jloc, red);
+    if (tid == 0) atomicAdd(X.J + s, Js);
+}
+
 // ---------------------------------------------------------------------------
 // per-snapshot bookkeeping after a step
 // ---------------------------------------------------------------------------

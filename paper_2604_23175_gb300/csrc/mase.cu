@@ -118,12 +118,15 @@ int join_out(mase_handle *h) {
 
 template <class RG, class RS>
 void setup_attrs(mase_handle *h) {
-    cudaFuncSetAttribute(k_local<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
+    cudaFuncSetAttribute(k_local<RG, RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
+    cudaFuncSetAttribute(k_local<RG, RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
     cudaFuncSetAttribute(k_back<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
     cudaFuncSetAttribute(k_boundary<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          h->smem_limit);
     cudaFuncSetAttribute(k_boundary_cl<RG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          h->smem_limit);
+    cudaFuncSetAttribute(k_objective<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
+    cudaFuncSetAttribute(k_objective<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_limit);
 }
 
 State make_state(mase_handle *h) {
@@ -166,14 +169,16 @@ inline void mark(mase_handle *h, int i) {
 template <class RG, class RS>
 void launch_local(mase_handle *h, const State &X, RG *fac, RS *cv, int *launches) {
     const int S = h->n_snap, K = h->S.K, nt = h->threads;
+    auto kern = h->vec_global ? k_local<RG, RS, true> : k_local<RG, RS, false>;
+    unsigned char *vs = h->vscratch.p;
     if (h->opt.schedule == MASE_BATCHED) {
-        k_local<RG, RS><<<K * S, nt, h->smem_local, h->stream>>>(h->d_areas.p, h->T, X, h->d_inst.p,
-                                                                -1, MODE_FULL, fac, cv, h->bh.p);
+        kern<<<K * S, nt, h->smem_local, h->stream>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1, fac, cv,
+                                                      h->bh.p, vs);
         ++*launches;
     } else {
         for (int k = 0; k < K; ++k) {
-            k_local<RG, RS><<<S, nt, h->areas_h[k].smem_bytes, h->stream>>>(
-                h->d_areas.p, h->T, X, nullptr, k, MODE_FULL, fac, cv, h->bh.p);
+            kern<<<S, nt, h->areas_h[k].smem_bytes, h->stream>>>(h->d_areas.p, h->T, X, nullptr, k, fac,
+                                                                 cv, h->bh.p, vs);
             ++*launches;
         }
     }
@@ -285,13 +290,8 @@ int build_loop_graph(mase_handle *h) {
     return MASE_OK;
 }
 
-template <class RG, class RS>
 int enqueue_objective(mase_handle *h, int *launches) {
-    State X = make_state(h);
-    k_local<RG, RS><<<h->S.K * h->n_snap, h->threads, h->smem_local, h->stream>>>(
-        h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (RG *)h->fac.p, (RS *)h->cvec.p,
-        h->bh.p);
-    ++*launches;
+    mase_internal::launch_objective(h, h->xV.p, h->xT.p, h->J.p, launches);
     return MASE_OK;
 }
 
@@ -354,21 +354,37 @@ int build(mase_handle *h) {
         d.off_st = (int)lay.off_st;
         const size_t o = lay.vector_bytes;
         const size_t with_st = o + (size_t)A.F.store_total * sizeof(RG);
+        const size_t ctr_bytes = ((2 * (size_t)A.F.nsn() + 1) * sizeof(int) + 15) & ~size_t(15);
+        d.vec_global = 0;
+        d.vec_stride = 0;
+        d.vec_base = 0;
         if (with_st <= (size_t)h->smem_limit) {
             d.in_smem = 1;
             d.smem_bytes = (int)with_st;
             ++in_smem_count;
-        } else {
+        } else if (o <= (size_t)h->smem_limit) {
             d.in_smem = 0;
             d.smem_bytes = (int)o;
+        } else {
+            // vectors and factor in global memory, dataflow counters on chip
+            if (ctr_bytes > (size_t)h->smem_limit)
+                return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large: task counters exceed shared memory");
+            d.in_smem = 0;
+            d.vec_global = 1;
+            d.smem_bytes = (int)ctr_bytes;
+            d.vec_stride = (int)((o + 255) & ~size_t(255));
+            d.vec_base = h->vscratch_bytes;
+            h->vscratch_bytes += (long long)d.vec_stride * nS;
+            h->vec_global = 1;
         }
-        if (o > (size_t)h->smem_limit)
-            return set_err(MASE_EINVAL, "area " + std::to_string(k) + " too large for shared memory");
         // the factorisation's task counters reuse the bus-value region
-        if ((2 * (size_t)A.F.nsn() + 1) * sizeof(int) > 3 * (size_t)A.nb_loc * sizeof(double))
+        if (!d.vec_global && ctr_bytes > 3 * (size_t)A.nb_loc * sizeof(double))
             return set_err(MASE_EINVAL, "area " + std::to_string(k) + ": task counters do not fit");
         max_local = std::max(max_local, (size_t)d.smem_bytes);
         d.back_smem_bytes = (int)(((size_t)nv * sizeof(RS) + 15) & ~size_t(15));
+        d.obj_off_end = (int)((3 * (size_t)A.nb_loc * sizeof(double) + 15) & ~size_t(15));
+        d.obj_smem_bytes = d.obj_off_end + 16 * A.n_ends;
+        if (!d.vec_global) h->smem_obj = std::max(h->smem_obj, (size_t)d.obj_smem_bytes);
         max_back = std::max(max_back, (size_t)d.back_smem_bytes);
         d.fac_base = fac_off;
         // instance bases stay 16-byte aligned
@@ -518,6 +534,7 @@ int build(mase_handle *h) {
     T.lev_chunks = h->t_lev_chunks.p;
     // work buffers
     CK(h->fac.alloc((size_t)h->fac_elems * sizeof(RG)));
+    CK(h->vscratch.alloc((size_t)std::max<long long>(16, h->vscratch_bytes)));
     CK(h->cvec.alloc((size_t)std::max<long long>(1, h->c_elems) * sizeof(RS)));
     CK(h->bh.alloc((size_t)std::max<long long>(1, h->bh_elems)));
     CK(h->bst.alloc((size_t)std::max(1, B.F.store_total) * nS * sizeof(RG)));
@@ -653,7 +670,7 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         }
     }
     CK(cudaEventRecord(ev[4], st));
-    int rc = enqueue_objective<RG, RS>(h, &launches);
+    int rc = enqueue_objective(h, &launches);
     if (rc != MASE_OK) return rc;
     if (x_out) {
         if (is_device_ptr(x_out)) {
@@ -1000,15 +1017,9 @@ void launch_objective(mase_handle *h, double *xV, double *xT, double *J, int *la
     X.xV = xV;
     X.xT = xT;
     X.J = J;
-    const int grid = h->S.K * h->n_snap;
-    if (h->opt.precision == MASE_MIXED)
-        k_local<float, float><<<grid, h->threads, h->smem_local, h->stream>>>(
-            h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (float *)h->fac.p,
-            (float *)h->cvec.p, h->bh.p);
-    else
-        k_local<double, double><<<grid, h->threads, h->smem_local, h->stream>>>(
-            h->d_areas.p, h->T, X, h->d_inst.p, -1, MODE_OBJECTIVE, (double *)h->fac.p,
-            (double *)h->cvec.p, h->bh.p);
+    auto kern = h->vec_global ? k_objective<true> : k_objective<false>;
+    kern<<<h->S.K * h->n_snap, 256, h->smem_obj, h->stream>>>(h->d_areas.p, h->T, X, h->d_inst.p,
+                                                               h->vscratch.p);
     if (launches) ++*launches;
 }
 

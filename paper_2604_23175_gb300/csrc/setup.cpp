@@ -686,8 +686,13 @@ bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st,
                                                         (int)own[k].size(), 4, 4);
                 const long long budget =
                     ((long long)smem_limit - (long long)lay.vector_bytes) / 4;
-                if (sym[k].F.store_total > budget) sym[k] = build_symbolic(sys, 0.10, 8);
-                if (sym[k].F.store_total > budget) sym[k] = build_symbolic(sys, 0.0, 0);
+                // less relaxation only when it brings the factor on chip; a factor
+                // that stays in global memory keeps the wider panels (fewer tasks)
+                if (budget > 0 && sym[k].F.store_total > budget) {
+                    SymResult alt = build_symbolic(sys, 0.10, 8);
+                    if (alt.F.store_total > budget) alt = build_symbolic(sys, 0.0, 0);
+                    if (alt.F.store_total <= budget) sym[k] = std::move(alt);
+                }
             }
             for (int i = 0; i < (int)nd.size(); ++i) node_of[nd[i]] = -1;
             // internal numbering: internal buses in elimination order, then own boundary buses

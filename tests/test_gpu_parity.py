@@ -269,3 +269,23 @@ def test_bounded_wait_gives_up_with_device_status(mase):
     x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED)
     assert res.rc == mase.MASE_OK
     _check(net, g, x, res, z, w, [0])
+
+
+def _one_area(g):
+    return synth.Grid(g.n_bus, g.from_bus, g.to_bus, g.r, g.x, g.b_charge,
+                      np.zeros(g.n_bus, dtype=np.int32), 1, g.slack, g.name + "_central")
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_parity_centralised_one_area(mase, precision):
+    """Centralised GPU Gauss-Newton: the whole network as one area (no
+    boundary, no coordinator), its gain matrix factored as one sparse
+    supernodal Cholesky with vectors and factor in global memory.  The
+    paper's "centralized GPU" baseline (Sec. 5.1); same estimates as the
+    oracle, and in FP64 the same iteration counts."""
+    g = _one_area(synth.make_grid("grid2869_k16"))
+    net, Vm, Va, z, sig = problem(g, 2, 4400)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=getattr(mase, precision), schedule=mase.BATCHED)
+    assert res.rc == mase.MASE_OK, (res.rc, res.status)
+    _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
