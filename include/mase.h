@@ -128,6 +128,14 @@ typedef struct {
                             boundary state held fixed before each condensed
                             step (Eq. local_wls); 0 = the exact condensed
                             step alone, whose iterates equal centralised GN */
+    int32_t autotune;    /* 1 (default): with MASE_BATCHED, mase_create times
+                            candidate launch configurations on the device (on
+                            a synthetic flat-start problem, so it needs no
+                            measurements) and keeps the fastest: the split of
+                            the areas into concurrent launch classes by the
+                            shared memory they need and the block size of
+                            each class, the back-substitution block size and
+                            the coordinator's form; mase_info reports them   */
 } mase_options;
 
 /* Per-solve results.  Arrays are host arrays of n_snap entries supplied by
@@ -172,6 +180,16 @@ typedef struct {
                                                Schur-block entries of one snapshot */
     int64_t coord_b_elems;                  /* sum over areas of nb(k): condensed rhs
                                                entries of one snapshot */
+    /* launch configuration (chosen by the autotuner when options.autotune) */
+    int32_t tuned;                          /* 1: measured at create */
+    int32_t local_classes;                  /* concurrent launch classes of the area kernel */
+    int32_t class_areas[4];                 /* areas in each class */
+    int32_t class_threads[4];               /* threads per block of each class */
+    int32_t class_smem[4];                  /* dynamic shared memory per block of each class */
+    int32_t back_threads;                   /* threads per block of the back-substitution */
+    int32_t coord_cluster;                  /* 1: coordinator on 2-block clusters */
+    float   tune_local_ms[2];               /* area-kernel time of one step on the tuning problem:
+                                               one launch for every area, and the chosen classes */
 } mase_info;
 
 /* Default options: MIXED, BATCHED, graph on, one FP64 refinement sweep of the
@@ -230,6 +248,11 @@ int mase_selfcheck(const mase_network *net, const mase_partition *part, uint64_t
 
 /* Message of the last mase_analyze / mase_selfcheck failure on this thread. */
 const char *mase_analyze_error(void);
+
+/* Host-only: sizeof of mase_options, mase_stats, mase_info and
+ * mase_warmstart_options as compiled into the library, so that bindings in
+ * other languages can check their copies of these structs. */
+void mase_abi_sizes(int64_t *sizes4);
 
 /* Coordinator step without device allocation.  The paper has no counterpart:
  * this entry point serves callers that cannot call cudaMalloc when they need

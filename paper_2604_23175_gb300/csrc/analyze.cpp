@@ -76,4 +76,12 @@ int mase_selfcheck(const mase_network *net, const mase_partition *part, uint64_t
 
 const char *mase_analyze_error(void) { return g_analyze_error.c_str(); }
 
+void mase_abi_sizes(int64_t *sizes4) {
+    if (!sizes4) return;
+    sizes4[0] = (int64_t)sizeof(mase_options);
+    sizes4[1] = (int64_t)sizeof(mase_stats);
+    sizes4[2] = (int64_t)sizeof(mase_info);
+    sizes4[3] = (int64_t)sizeof(mase_warmstart_options);
+}
+
 }  // extern "C"

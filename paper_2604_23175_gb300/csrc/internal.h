@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,16 @@ using mase_dev::BndDev;
 using mase_dev::StopRule;
 using mase_dev::Tables;
 
+// One launch of the area kernel over a class of (area, snapshot) instances
+// that share a block size and a dynamic shared-memory size.
+struct LocalClass {
+    int threads = 512;
+    size_t smem = 0;
+    int n_areas = 0;
+    std::vector<int2> inst_h;
+    DevBuf<int2> inst;
+};
+
 struct mase_handle {
     mase::Setup S;
     mase_options opt{};
@@ -111,6 +122,12 @@ struct mase_handle {
     DevBuf<unsigned long long> maxstep;
     int *h_n_active = nullptr;   // pinned
     size_t smem_local = 0, smem_back = 0, smem_bnd = 0, smem_obj = 0;
+    // launch configuration (autotuned at create when options.autotune)
+    std::vector<std::unique_ptr<LocalClass>> lcls;   // area-kernel launch classes
+    std::vector<int> area_order;                     // areas by descending estimated work
+    int back_threads = 256;
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // concurrent class launches
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     // areas whose vectors live in global scratch (one area holding a large network)
     int vec_global = 0;
     long long vscratch_bytes = 0;
@@ -154,6 +171,11 @@ struct mase_handle {
         for (auto &e : ev_stage)
             if (e) cudaEventDestroy(e);
         if (stream) cudaStreamDestroy(stream);
+        for (auto &q : side)
+            if (q) cudaStreamDestroy(q);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (auto &e : ev_join)
+            if (e) cudaEventDestroy(e);
     }
 };
 

@@ -21,6 +21,8 @@ namespace {
 // the back-substitution is a gather over a few warps' worth of rows per
 // level; 256 threads measured faster than 512 on the 9241-bus workload
 constexpr int kBackThreads = 256;
+// shared memory of one SM that blocks can use (228 KB, less 1 KB each)
+constexpr size_t kSmemPerSM = 228 * 1024;
 
 thread_local std::string g_last_error;
 
@@ -167,14 +169,32 @@ inline void mark(mase_handle *h, int i) {
 }
 
 template <class RG, class RS>
+void launch_class(mase_handle *h, const State &X, RG *fac, RS *cv, const LocalClass &c, cudaStream_t st) {
+    auto kern = h->vec_global ? k_local<RG, RS, true> : k_local<RG, RS, false>;
+    kern<<<(int)c.inst_h.size(), c.threads, c.smem, st>>>(h->d_areas.p, h->T, X, c.inst.p, -1, fac, cv,
+                                                         h->bh.p, h->vscratch.p);
+}
+
+// The area kernel over every (area, snapshot): one launch per class, the
+// classes on forked streams so that they share the GPU.
+template <class RG, class RS>
 void launch_local(mase_handle *h, const State &X, RG *fac, RS *cv, int *launches) {
     const int S = h->n_snap, K = h->S.K, nt = h->threads;
     auto kern = h->vec_global ? k_local<RG, RS, true> : k_local<RG, RS, false>;
     unsigned char *vs = h->vscratch.p;
     if (h->opt.schedule == MASE_BATCHED) {
-        kern<<<K * S, nt, h->smem_local, h->stream>>>(h->d_areas.p, h->T, X, h->d_inst.p, -1, fac, cv,
-                                                      h->bh.p, vs);
-        ++*launches;
+        const int nc = (int)h->lcls.size();
+        if (nc > 1) {
+            cudaEventRecord(h->ev_fork, h->stream);
+            for (int c = 1; c < nc; ++c) {
+                cudaStreamWaitEvent(h->side[c - 1], h->ev_fork, 0);
+                launch_class<RG, RS>(h, X, fac, cv, *h->lcls[c], h->side[c - 1]);
+                cudaEventRecord(h->ev_join[c - 1], h->side[c - 1]);
+            }
+        }
+        launch_class<RG, RS>(h, X, fac, cv, *h->lcls[0], h->stream);
+        for (int c = 1; c < nc; ++c) cudaStreamWaitEvent(h->stream, h->ev_join[c - 1], 0);
+        *launches += nc;
     } else {
         for (int k = 0; k < K; ++k) {
             kern<<<S, nt, h->areas_h[k].smem_bytes, h->stream>>>(h->d_areas.p, h->T, X, nullptr, k, fac,
@@ -189,13 +209,13 @@ void launch_back(mase_handle *h, const State &X, const RG *fac, const RS *cv, co
                  int *launches) {
     const int S = h->n_snap, K = h->S.K;
     if (h->opt.schedule == MASE_BATCHED) {
-        k_back<RG, RS><<<K * S, kBackThreads, h->smem_back, h->stream>>>(
+        k_back<RG, RS><<<K * S, h->back_threads, h->smem_back, h->stream>>>(
             h->d_areas.p, h->T, X, h->d_inst.p, -1, fac, cv, dxG, h->bnd.n_gamma);
         ++*launches;
     } else {
         for (int k = 0; k < K; ++k) {
             const size_t sm = (size_t)h->areas_h[k].back_smem_bytes;
-            k_back<RG, RS><<<S, kBackThreads, sm, h->stream>>>(h->d_areas.p, h->T, X, nullptr, k, fac,
+            k_back<RG, RS><<<S, h->back_threads, sm, h->stream>>>(h->d_areas.p, h->T, X, nullptr, k, fac,
                                                                cv, dxG, h->bnd.n_gamma);
             ++*launches;
         }
@@ -454,6 +474,15 @@ int build(mase_handle *h) {
     h->inst_h.clear();
     for (int k : ord)
         for (int s = 0; s < nS; ++s) h->inst_h.push_back(make_int2(k, s));
+    // default launch configuration: one class holding every area
+    h->area_order = ord;
+    h->lcls.clear();
+    h->lcls.emplace_back(new LocalClass());
+    h->lcls[0]->threads = h->threads;
+    h->lcls[0]->smem = h->smem_local;
+    h->lcls[0]->n_areas = K;
+    h->lcls[0]->inst_h = h->inst_h;
+    h->back_threads = kBackThreads;
     // uploads
 #define UP(buf, vec) CK(h->buf.upload(H.vec, st))
     UP(t_sn_c0, sn_c0); UP(t_sn_w, sn_w); UP(t_sn_nr, sn_nr); UP(t_sn_off, sn_off);
@@ -508,6 +537,7 @@ int build(mase_handle *h) {
     std::vector<AreaDev> ah = h->areas_h;
     CK(h->d_areas.upload(ah, st));
     CK(h->d_inst.upload(h->inst_h, st));
+    CK(h->lcls[0]->inst.upload(h->lcls[0]->inst_h, st));
     Tables &T = h->T;
     // a dependency wait gives up after this many unsatisfied polls (~0.2 s by default)
     T.wait_polls = h->opt.wait_polls > 0 ? h->opt.wait_polls : (1 << 22);
@@ -563,6 +593,158 @@ int build(mase_handle *h) {
     I.areas_in_smem = in_smem_count;
     I.boundary_store = B.F.store_total;
     I.boundary_levels = B.F.nlev();
+    return MASE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: the launch configuration measured on the device at create
+// ---------------------------------------------------------------------------
+// Best of `reps` timings (CUDA events on the library's stream) after one
+// untimed run.
+template <class F>
+float time_min(mase_handle *h, F fn, int reps) {
+    fn();
+    float best = 1e30f;
+    for (int i = 0; i < reps; ++i) {
+        cudaEventRecord(h->ev_solve[0], h->stream);
+        fn();
+        cudaEventRecord(h->ev_solve[1], h->stream);
+        cudaEventSynchronize(h->ev_solve[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_solve[0], h->ev_solve[1]);
+        best = std::min(best, ms);
+    }
+    return best;
+}
+
+// The tuning problem is the network at the flat start with z = h(x_flat) in
+// every snapshot: the same sparsity, task lists and instance counts as any
+// batch of real measurements, so the timings carry over, and no measurement
+// of the caller is needed.  Candidates:
+//  * area-to-block packing: areas grouped into classes by how many of their
+//    blocks fit on one SM by shared memory (1, 2, 3+), each class launched
+//    on its own stream with its own dynamic shared memory; per class the
+//    block size is chosen among those whose registers still allow that many
+//    blocks per SM; the split is kept only if it beats one launch for all;
+//  * block size of the back-substitution;
+//  * coordinator on 2-block clusters or on one block (factor top on chip).
+template <class RG, class RS>
+int autotune(mase_handle *h) {
+    mase_info &I = h->info;
+    I.local_classes = 1;
+    I.class_areas[0] = h->S.K;
+    I.class_threads[0] = h->threads;
+    I.class_smem[0] = (int)h->smem_local;
+    I.back_threads = h->back_threads;
+    I.coord_cluster = h->bnd_cluster;
+    if (h->opt.schedule != MASE_BATCHED || !h->opt.autotune) return MASE_OK;
+    cudaStream_t st = h->stream;
+    const int K = h->S.K, nS = h->n_snap, M = h->S.m, N = h->S.N;
+    for (int s = 0; s < nS; ++s)
+        CK(cudaMemcpyAsync(h->z_int.p + (size_t)s * M, h->h_flat.p, (size_t)M * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
+    State X = make_state(h);
+    X.mask = nullptr;
+    k_state_in<<<1024, 256, 0, st>>>(nullptr, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS, 1);
+    k_reset<<<(nS + 255) / 256, 256, 0, st>>>(X, h->iters.p, h->status.p, h->laststep.p, make_ctl(h));
+    CK(cudaGetLastError());
+    RG *fac = (RG *)h->fac.p;
+    RS *cv = (RS *)h->cvec.p;
+    int nl = 0;
+    auto run_local = [&]() { launch_local<RG, RS>(h, X, fac, cv, &nl); };
+    const float t_single = time_min(h, run_local, 3);
+    // classes by blocks per SM that fit by shared memory, in descending-work order
+    std::vector<std::vector<int>> by_cap(4);
+    for (int k : h->area_order) {
+        const size_t need = (size_t)h->areas_h[k].smem_bytes + 1024;
+        const int cap = (int)std::min<size_t>(3, std::max<size_t>(1, kSmemPerSM / need));
+        by_cap[cap].push_back(k);
+    }
+    std::vector<std::unique_ptr<LocalClass>> single;
+    single.swap(h->lcls);
+    std::vector<int> caps;
+    for (int cap = 1; cap <= 3; ++cap) {
+        if (by_cap[cap].empty()) continue;
+        caps.push_back(cap);
+        std::unique_ptr<LocalClass> c(new LocalClass());
+        c->n_areas = (int)by_cap[cap].size();
+        for (int k : by_cap[cap]) {
+            c->smem = std::max(c->smem, (size_t)h->areas_h[k].smem_bytes);
+            for (int s = 0; s < nS; ++s) c->inst_h.push_back(make_int2(k, s));
+        }
+        CK(c->inst.upload(c->inst_h, st));
+        c->threads = h->threads;
+        h->lcls.push_back(std::move(c));
+    }
+    float t_split = 1e30f;
+    if (h->lcls.size() > 1 || (caps.size() == 1 && caps[0] > 1)) {
+        // block size per class, the class timed alone
+        for (size_t ci = 0; ci < h->lcls.size(); ++ci) {
+            LocalClass &c = *h->lcls[ci];
+            const int cap = caps[ci];
+            int best_t = h->threads;
+            float best = 1e30f;
+            for (int t : {512, 256, 160}) {
+                if (t > h->threads || (t != h->threads && (long long)t * cap > 512)) continue;
+                c.threads = t;
+                const float ms = time_min(h, [&]() { launch_class<RG, RS>(h, X, fac, cv, c, st); }, 3);
+                if (ms < best) {
+                    best = ms;
+                    best_t = t;
+                }
+            }
+            c.threads = best_t;
+        }
+        t_split = time_min(h, run_local, 3);
+    }
+    CK(cudaGetLastError());
+    if (!(t_split < 0.99f * t_single)) {
+        h->lcls.swap(single);   // one launch for every area stays
+        t_split = t_single;
+    }
+    // back-substitution block size
+    launch_local<RG, RS>(h, X, fac, cv, &nl);
+    {
+        int best_t = h->back_threads;
+        float best = 1e30f;
+        for (int t : {256, 128}) {
+            h->back_threads = t;
+            const float ms = time_min(h, [&]() { launch_back<RG, RS>(h, X, fac, cv, h->dx_zero.p, &nl); }, 3);
+            if (ms < best) {
+                best = ms;
+                best_t = t;
+            }
+        }
+        h->back_threads = best_t;
+    }
+    // coordinator form
+    if (h->bnd.n_gamma > 0 && h->bnd_cluster) {
+        const int refine = h->opt.precision == MASE_MIXED ? h->opt.refine : 0;
+        const int nt = h->threads;
+        const float t_cl = time_min(h, [&]() {
+            k_boundary_cl<RG, RS><<<2 * nS, nt, h->smem_bnd_cl, st>>>(h->T, X, h->bnd, fac, h->bh.p,
+                                                                    (RG *)h->bA.p, h->dxG.p, refine);
+        }, 3);
+        const float t_one = time_min(h, [&]() {
+            k_boundary<RG, RS><<<nS, nt, h->smem_bnd, st>>>(h->d_areas.p, h->T, X, h->bnd, fac, h->bh.p,
+                                                           (RG *)h->bst.p, (RG *)h->bA.p, h->dxG.p, refine);
+        }, 3);
+        h->bnd_cluster = t_cl <= t_one ? 1 : 0;
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    I.tuned = 1;
+    I.local_classes = (int)h->lcls.size();
+    for (int c = 0; c < 4; ++c) I.class_areas[c] = I.class_threads[c] = I.class_smem[c] = 0;
+    for (size_t c = 0; c < h->lcls.size() && c < 4; ++c) {
+        I.class_areas[c] = h->lcls[c]->n_areas;
+        I.class_threads[c] = h->lcls[c]->threads;
+        I.class_smem[c] = (int)h->lcls[c]->smem;
+    }
+    I.back_threads = h->back_threads;
+    I.coord_cluster = h->bnd_cluster;
+    I.tune_local_ms[0] = t_single;
+    I.tune_local_ms[1] = t_split;
     return MASE_OK;
 }
 
@@ -752,6 +934,7 @@ void mase_default_options(mase_options *o) {
     o->profile = 0;
     o->wait_polls = 0;
     o->inner_iters = 0;
+    o->autotune = 1;
 }
 
 const char *mase_status_str(int code) {
@@ -808,6 +991,9 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     for (auto &e : h->ev_solve) CK(cudaEventCreate(&e));
     for (auto &e : h->ev_stage) CK(cudaEventCreate(&e));
+    for (auto &q : h->side) CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    for (auto &e : h->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     {
         int rc0 = join_in(h.get());
         if (rc0 != MASE_OK) return rc0;
@@ -895,6 +1081,8 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
         CK(h->m_inc_beg.upload(beg, st));
         CK(h->m_inc_br.upload(br, st));
     }
+    rc = h->opt.precision == MASE_MIXED ? autotune<float, float>(h.get()) : autotune<double, double>(h.get());
+    if (rc != MASE_OK) return rc;
     rc = upload_measurements(h.get(), meas);
     if (rc != MASE_OK) return rc;
     CK(cudaStreamSynchronize(st));

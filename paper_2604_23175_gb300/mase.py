@@ -45,7 +45,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
                 ("stream", C.c_void_p), ("profile", C.c_int32), ("wait_polls", C.c_int32),
-                ("inner_iters", C.c_int32)]
+                ("inner_iters", C.c_int32), ("autotune", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -70,10 +70,17 @@ class Info(C.Structure):
                 ("n_supernodes", C.c_int64), ("n_units", C.c_int64), ("max_levels", C.c_int32),
                 ("max_area_store", C.c_int32), ("boundary_store", C.c_int32),
                 ("boundary_levels", C.c_int32), ("coord_S_elems", C.c_int64),
-                ("coord_b_elems", C.c_int64)]
+                ("coord_b_elems", C.c_int64), ("tuned", C.c_int32), ("local_classes", C.c_int32),
+                ("class_areas", C.c_int32 * 4), ("class_threads", C.c_int32 * 4),
+                ("class_smem", C.c_int32 * 4), ("back_threads", C.c_int32),
+                ("coord_cluster", C.c_int32), ("tune_local_ms", C.c_float * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if hasattr(v, "_length_") else v
+        return out
 
 
 _lib = None
@@ -109,6 +116,7 @@ def load() -> C.CDLL:
         "mase_analyze": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.POINTER(Info)]),
         "mase_selfcheck": (C.c_int, [C.POINTER(Network), C.POINTER(Partition), C.c_uint64, _f64p]),
         "mase_analyze_error": (C.c_char_p, []),
+        "mase_abi_sizes": (None, [C.POINTER(C.c_int64)]),
         "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                                C.c_void_p, C.c_int64]),
         "mase_warmstart_default_options": (None, [C.POINTER(WarmstartOptions)]),
@@ -131,6 +139,14 @@ def load() -> C.CDLL:
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def abi_sizes() -> dict:
+    """sizeof of the C structs in the library against this binding's copies."""
+    out = (C.c_int64 * 4)()
+    load().mase_abi_sizes(out)
+    return {"options": (out[0], C.sizeof(Options)), "stats": (out[1], C.sizeof(Stats)),
+            "info": (out[2], C.sizeof(Info)), "warmstart_options": (out[3], C.sizeof(WarmstartOptions))}
 
 
 def status_str(code: int) -> str:
@@ -245,7 +261,7 @@ class Estimator:
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
                  schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
-                 profile=False, wait_polls=0, inner_iters=0):
+                 profile=False, wait_polls=0, inner_iters=0, autotune=True):
         self.lib = load()
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -256,6 +272,7 @@ class Estimator:
         opt.profile = int(bool(profile))
         opt.wait_polls = int(wait_polls)
         opt.inner_iters = int(inner_iters)
+        opt.autotune = int(bool(autotune))
         meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
         h = C.c_void_p()
         rc = self.lib.mase_create(C.byref(net), C.byref(part), C.byref(meas), C.byref(opt), C.byref(h))

@@ -319,16 +319,21 @@ def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
     """Presence mask [n_snap][m] (1 = present) dropping ``drop_frac`` of rows
     per snapshot uniformly at random; a snapshot is redrawn if some bus is
     left with fewer than ``min_present`` present rows that touch it."""
+    import scipy.sparse as sp
     rng = np.random.Generator(np.random.PCG64(seed))
     m = grid.n_meas
     touch = rows_touching_bus(grid)
+    # bus x row incidence of "row touches bus": present-row counts are one product
+    cols = np.concatenate(touch)
+    rows = np.repeat(np.arange(grid.n_bus), [len(t) for t in touch])
+    inc = sp.csr_matrix((np.ones(len(cols), dtype=np.int32), (rows, cols)), shape=(grid.n_bus, m))
     k = int(round(drop_frac * m))
     out = np.ones((n_snap, m), dtype=np.uint8)
     for s in range(n_snap):
         for _ in range(100):
             row = np.ones(m, dtype=np.uint8)
             row[rng.choice(m, size=k, replace=False)] = 0
-            if all(int(row[t].sum()) >= min_present for t in touch):
+            if int((inc @ row.astype(np.int32)).min()) >= min_present:
                 break
         else:
             raise RuntimeError("could not draw an observable mask")

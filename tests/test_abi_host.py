@@ -45,11 +45,17 @@ def test_library_exports_every_declared_symbol(mase):
         assert hasattr(lib, n), n
 
 
+def test_struct_layouts_match_the_library(mase):
+    for name, (c_size, py_size) in mase.abi_sizes().items():
+        assert c_size == py_size, (name, c_size, py_size)
+
+
 def test_status_strings_and_defaults(mase):
     assert mase.status_str(0) == "MASE_OK"
     assert mase.status_str(-2) == "MASE_EUNOBSERVABLE"
     o = mase.default_options()
     assert o.precision == mase.MIXED and o.schedule == mase.BATCHED and o.refine == 1 and o.inner_iters == 0
+    assert o.autotune == 1 and o.profile == 0 and o.wait_polls == 0
 
 
 @pytest.mark.parametrize("name", ["grid300_k4", "grid2869_k16", "grid9241_k32"])

@@ -289,3 +289,31 @@ def test_parity_centralised_one_area(mase, precision):
     x, res = _run(mase, g, sig, z, precision=getattr(mase, precision), schedule=mase.BATCHED)
     assert res.rc == mase.MASE_OK, (res.rc, res.status)
     _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
+
+
+def test_autotuner_reports_a_valid_configuration(mase):
+    """With autotune (the default) mase_create measures the launch
+    configuration and reports it; the classes cover every area once, each
+    within the block-size and shared-memory limits; without autotune one
+    launch holds every area.  Both configurations give the oracle's
+    estimates (every other parity test also runs tuned handles)."""
+    g = synth.make_grid("grid2869_k16")
+    net, Vm, Va, z, sig = problem(g, 4, 4500)
+    w = wls.weights(sig)
+    for tune in (True, False):
+        est = mase.Estimator(g, sig, 4, z=z, precision=mase.MIXED, schedule=mase.BATCHED, autotune=tune)
+        info = est.info()
+        x = np.zeros((4, 2 * g.n_bus))
+        res = est.solve(tol=1e-8, max_iter=20, x_out=x)
+        est.close()
+        assert info["tuned"] == int(tune)
+        nc = info["local_classes"]
+        assert 1 <= nc <= 3
+        assert sum(info["class_areas"][:nc]) == g.n_area
+        for c in range(nc):
+            assert 64 <= info["class_threads"][c] <= 512 and info["class_threads"][c] % 32 == 0
+            assert 0 < info["class_smem"][c] <= 227 * 1024
+        if not tune:
+            assert nc == 1 and info["class_threads"][0] == 512
+        assert info["back_threads"] in (128, 256)
+        _check(net, g, x, res, z, w, range(4))
