@@ -67,6 +67,8 @@ def parse():
                     help="fraction of measurement rows dropped at random per snapshot")
     ap.add_argument("--areas", type=int, default=0,
                     help="split the workload's network into this many areas with the partitioner")
+    ap.add_argument("--inner-iters", type=int, default=0,
+                    help="local Gauss-Newton steps per area with the boundary fixed before each condensed step")
     return ap.parse_args()
 
 
@@ -288,7 +290,7 @@ def run_ours(args, dist):
     z_dev = torch.empty((S, g.n_meas), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     est = mase.Estimator(g, sig, S, z=None, precision=mase.MIXED, schedule=mase.BATCHED,
-                         use_graph=True, refine=1, device=dev, stream=stream)
+                         use_graph=True, refine=1, device=dev, stream=stream, inner_iters=args.inner_iters)
     est.measure(x_true, z_dev)
     z_dev += torch.tensor(e, device="cuda")
     z_host = z_dev.cpu().numpy().copy()
@@ -316,23 +318,30 @@ def run_ours(args, dist):
         t0 = time.perf_counter()
         Zs, Xs = [], []
         nb = max(1, args.train_samples // S)
+        # training states are solved with every row present (a mask set on
+        # the handle stays until replaced); snapshots that do not converge
+        # are left out of the training set
+        all_rows = torch.ones((S, g.n_meas), dtype=torch.uint8, device="cuda") if mask_dev is not None else None
+        left_out = 0
         for b in range(nb):
             Vt, At = synth.make_states(g, S, 30000 + 7 * b, walk_len=1)
             et = synth.make_noise(g, S, 30001 + 7 * b)
             zt = torch.empty((S, g.n_meas), dtype=torch.float64, device="cuda")
             est.measure(torch.tensor(np.concatenate([Vt, At], 1), device="cuda"), zt)
             zt += torch.tensor(et, device="cuda")
-            est.set_measurements(zt)
+            est.set_measurements(zt, all_rows)
             xt = torch.zeros((S, 2 * N), dtype=torch.float64, device="cuda")
-            est.solve(tol=TOL, max_iter=MAX_ITER, x_out=xt)
-            Zs.append(zt)
-            Xs.append(xt)
+            rt = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=xt, check=False)
+            ok = torch.tensor(rt.status == 0, device="cuda")
+            left_out += int(S - int(ok.sum().item()))
+            Zs.append(zt[ok])
+            Xs.append(xt[ok])
         t1 = time.perf_counter()
         loss = est.warmstart_train(torch.cat(Zs), torch.cat(Xs), epochs=args.train_epochs, batch=256, lr=1e-3)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         del Zs, Xs
-        warm = {"trained": True, "samples": nb * S, "epochs": args.train_epochs,
+        warm = {"trained": True, "samples": nb * S - left_out, "left_out": left_out, "epochs": args.train_epochs,
                 "final_loss": loss, "data_s": t1 - t0, "train_s": t2 - t1}
         est.set_measurements(z_dev, mask_dev)
         # iterations from the flat, previous-snapshot and learned starts
@@ -439,7 +448,8 @@ def run_ours(args, dist):
     # ---- per-stage kernel times with CUDA events (host-stepped, flat start:
     # every launch works on all snapshots, 6 steps), for the rooflines
     prof = mase.Estimator(g, sig, S, z=z_dev, mask=mask_dev, precision=mase.MIXED,
-                          schedule=mase.BATCHED, refine=1, device=dev, stream=stream, profile=True)
+                          schedule=mase.BATCHED, refine=1, device=dev, stream=stream, profile=True,
+                          inner_iters=args.inner_iters)
     pst, psteps, pact = np.zeros(7), 0, []
     for i in range(1 + 3):
         flush()
@@ -503,10 +513,12 @@ def run_ours(args, dist):
     x_fp64_h = x_fp64.cpu().numpy()
     cmp.close()
 
-    variant = bool(args.workload != WORKLOAD or S != 64 or args.areas or args.family or args.drop)
+    variant = bool(args.workload != WORKLOAD or S != 64 or args.areas or args.family or args.drop
+                   or args.inner_iters)
     desc = WORKLOAD_DESC if not variant else (
         f"{g.name} x{S} snapshots" + (f", {args.family} rows dropped" if args.family else "")
-        + (f", {100 * args.drop:g}% rows dropped at random" if args.drop else ""))
+        + (f", {100 * args.drop:g}% rows dropped at random" if args.drop else "")
+        + (f", {args.inner_iters} inner local steps" if args.inner_iters else ""))
     # every kernel of the library launched inside the timed region (all legs)
     launches = sum(r["launches"] for r in rec.values())
     out = {

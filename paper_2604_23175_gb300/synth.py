@@ -299,44 +299,76 @@ def make_noise(grid: Grid, n_snap: int, seed: int) -> np.ndarray:
     return rng.standard_normal((n_snap, sig.shape[0])) * sig
 
 
+def _rows_touching_bus_by_kind(grid: Grid):
+    """Rows whose function depends on each bus (structure only), split into
+    active-power rows (P injections at the bus and its neighbours, P flows on
+    incident branches) and reactive or voltage rows (Vm at the bus, Q
+    injections, Q flows)."""
+    N, L = grid.n_bus, grid.n_branch
+    p_rows = [[N + i] for i in range(N)]
+    q_rows = [[i, 2 * N + i] for i in range(N)]
+    base = 3 * N
+    for l in range(L):
+        f, t = int(grid.from_bus[l]), int(grid.to_bus[l])
+        pf = [base + l, base + 2 * L + l]
+        qf = [base + L + l, base + 3 * L + l]
+        p_rows[f] += pf + [N + t]
+        p_rows[t] += pf + [N + f]
+        q_rows[f] += qf + [2 * N + t]
+        q_rows[t] += qf + [2 * N + f]
+    return ([np.unique(np.asarray(v, dtype=np.int64)) for v in p_rows],
+            [np.unique(np.asarray(v, dtype=np.int64)) for v in q_rows])
+
+
 def rows_touching_bus(grid: Grid):
     """For each bus, the canonical rows whose function depends on that bus
     (structure only: Vm and injections at the bus and its neighbours, flows on
     incident branches).  Used to keep random masks observable."""
-    N, L = grid.n_bus, grid.n_branch
-    touch = [[i, N + i, 2 * N + i] for i in range(N)]
-    base = 3 * N
-    for l in range(L):
-        f, t = int(grid.from_bus[l]), int(grid.to_bus[l])
-        fam = [base + l, base + L + l, base + 2 * L + l, base + 3 * L + l]
-        touch[f] += fam + [N + t, 2 * N + t]
-        touch[t] += fam + [N + f, 2 * N + f]
-    return [np.unique(np.asarray(v, dtype=np.int64)) for v in touch]
+    return [np.union1d(p, q) for p, q in zip(*_rows_touching_bus_by_kind(grid))]
 
 
 def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
               min_present: int = 4) -> np.ndarray:
     """Presence mask [n_snap][m] (1 = present) dropping ``drop_frac`` of rows
-    per snapshot uniformly at random; a snapshot is redrawn if some bus is
-    left with fewer than ``min_present`` present rows that touch it."""
+    per snapshot uniformly at random, then repaired so that every bus keeps
+    at least one present active-power row and one present reactive/voltage
+    row touching it, and at least ``min_present`` touching rows in all:
+    where a bus falls short, dropped rows of the missing kind touching it are
+    restored, drawn at random.  (A tree-leaf bus left with active-power rows
+    only has all of them on its one branch; at the flat start they fix one
+    combination of its magnitude and angle, and its gain block is singular.)
+    The repair restores a handful of rows per snapshot, so the dropped
+    fraction stays within a few thousandths of a percent of ``drop_frac``."""
     import scipy.sparse as sp
     rng = np.random.Generator(np.random.PCG64(seed))
     m = grid.n_meas
-    touch = rows_touching_bus(grid)
-    # bus x row incidence of "row touches bus": present-row counts are one product
-    cols = np.concatenate(touch)
-    rows = np.repeat(np.arange(grid.n_bus), [len(t) for t in touch])
-    inc = sp.csr_matrix((np.ones(len(cols), dtype=np.int32), (rows, cols)), shape=(grid.n_bus, m))
+    p_rows, q_rows = _rows_touching_bus_by_kind(grid)
+    all_rows = [np.union1d(p, q) for p, q in zip(p_rows, q_rows)]
+
+    def incidence(lists):
+        cols = np.concatenate(lists)
+        rows = np.repeat(np.arange(grid.n_bus), [len(t) for t in lists])
+        return sp.csr_matrix((np.ones(len(cols), dtype=np.int32), (rows, cols)), shape=(grid.n_bus, m))
+
+    checks = [(incidence(p_rows), p_rows, 1), (incidence(q_rows), q_rows, 1),
+              (incidence(all_rows), all_rows, min_present)]
     k = int(round(drop_frac * m))
     out = np.ones((n_snap, m), dtype=np.uint8)
     for s in range(n_snap):
-        for _ in range(100):
-            row = np.ones(m, dtype=np.uint8)
-            row[rng.choice(m, size=k, replace=False)] = 0
-            if int((inc @ row.astype(np.int32)).min()) >= min_present:
+        row = np.ones(m, dtype=np.uint8)
+        row[rng.choice(m, size=k, replace=False)] = 0
+        for _ in range(8):
+            short = False
+            for inc, lists, need in checks:
+                cnt = inc @ row.astype(np.int32)
+                for b in np.nonzero(cnt < need)[0].tolist():
+                    dropped = lists[b][row[lists[b]] == 0]
+                    take = min(len(dropped), int(need - cnt[b]))
+                    if take > 0:
+                        row[rng.choice(dropped, size=take, replace=False)] = 1
+                    short = True
+            if not short:
                 break
-        else:
-            raise RuntimeError("could not draw an observable mask")
         out[s] = row
     return out
 
