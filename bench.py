@@ -67,6 +67,8 @@ def parse():
                     help="fraction of measurement rows dropped at random per snapshot")
     ap.add_argument("--areas", type=int, default=0,
                     help="split the workload's network into this many areas with the partitioner")
+    ap.add_argument("--max-iter", type=int, default=MAX_ITER,
+                    help="Gauss-Newton step cap per snapshot")
     ap.add_argument("--inner-iters", type=int, default=0,
                     help="local Gauss-Newton steps per area with the boundary fixed before each condensed step")
     return ap.parse_args()
@@ -318,10 +320,19 @@ def run_ours(args, dist):
         t0 = time.perf_counter()
         Zs, Xs = [], []
         nb = max(1, args.train_samples // S)
-        # training states are solved with every row present (a mask set on
-        # the handle stays until replaced); snapshots that do not converge
-        # are left out of the training set
+        # training snapshots see the benchmark's kind of drops: under random
+        # drops each training batch draws its own masks (four batches of
+        # masks, reused in turn), is solved under them and trains the
+        # networks with them; a family mask is the same for every batch.
+        # Snapshots that do not converge are left out of the training set.
         all_rows = torch.ones((S, g.n_meas), dtype=torch.uint8, device="cuda") if mask_dev is not None else None
+        train_masks = []
+        if mask_dev is not None and not args.family:
+            train_masks = [torch.tensor(synth.make_mask(g, S, args.drop, 40000 + 7 * b), device="cuda")
+                           for b in range(min(nb, 4))]
+        elif mask_dev is not None:
+            train_masks = [mask_dev]
+        Ms = []
         left_out = 0
         for b in range(nb):
             Vt, At = synth.make_states(g, S, 30000 + 7 * b, walk_len=1)
@@ -329,19 +340,24 @@ def run_ours(args, dist):
             zt = torch.empty((S, g.n_meas), dtype=torch.float64, device="cuda")
             est.measure(torch.tensor(np.concatenate([Vt, At], 1), device="cuda"), zt)
             zt += torch.tensor(et, device="cuda")
-            est.set_measurements(zt, all_rows)
+            mt = train_masks[b % len(train_masks)] if train_masks else all_rows
+            est.set_measurements(zt, mt)
             xt = torch.zeros((S, 2 * N), dtype=torch.float64, device="cuda")
             rt = est.solve(tol=TOL, max_iter=MAX_ITER, x_out=xt, check=False)
             ok = torch.tensor(rt.status == 0, device="cuda")
             left_out += int(S - int(ok.sum().item()))
             Zs.append(zt[ok])
             Xs.append(xt[ok])
+            if train_masks:
+                Ms.append(mt[ok])
         t1 = time.perf_counter()
-        loss = est.warmstart_train(torch.cat(Zs), torch.cat(Xs), epochs=args.train_epochs, batch=256, lr=1e-3)
+        loss = est.warmstart_train(torch.cat(Zs), torch.cat(Xs), epochs=args.train_epochs, batch=256, lr=1e-3,
+                                   mask=torch.cat(Ms) if Ms else None)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        del Zs, Xs
+        del Zs, Xs, Ms
         warm = {"trained": True, "samples": nb * S - left_out, "left_out": left_out, "epochs": args.train_epochs,
+                "masked_training": bool(train_masks),
                 "final_loss": loss, "data_s": t1 - t0, "train_s": t2 - t1}
         est.set_measurements(z_dev, mask_dev)
         # iterations from the flat, previous-snapshot and learned starts
@@ -357,7 +373,7 @@ def run_ours(args, dist):
         warm.update({"iters_flat": float(rf.iters.mean()), "iters_prev": float(rp.iters.mean()),
                      "iters_learned": float(rl.iters.mean()),
                      "iters_max_flat": int(rf.iters.max()), "iters_max_prev": int(rp.iters.max()),
-                     "iters_max_learned": int(rl.iters.max()),
+                     "iters_max_learned": int(rl.iters.max()), "flat_fallbacks_learned": rl.restarted,
                      "max_state_diff_learned_vs_flat": float((x_dev - x_flat).abs().max().item())})
 
     # ---- the timed legs
@@ -368,7 +384,8 @@ def run_ours(args, dist):
     for sname, smode in starts:
         legs[f"device_{sname}"] = (smode, False)
         legs[f"e2e_{sname}"] = (smode, True)
-    rec = {k: {"ms": [], "solve_ms": [], "stages": [], "launches": 0, "iters": [], "round": []} for k in legs}
+    rec = {k: {"ms": [], "solve_ms": [], "stages": [], "launches": 0, "iters": [], "round": [], "restarted": 0}
+           for k in legs}
 
     def run_leg(name, n, timed, rnd=0):
         smode, e2e = legs[name]
@@ -394,6 +411,7 @@ def run_ours(args, dist):
                 r["launches"] += res.launches + 1 + (1 if mask_dev is not None else 0)
                 r["iters"].append(res.iters.copy())
                 r["round"].append(rnd)
+                r["restarted"] += res.restarted
         return res
 
     for name in legs:
@@ -430,7 +448,8 @@ def run_ours(args, dist):
                 "iters_max": int(np.max(np.concatenate(r["iters"]))),
                 "stages_ms_per_step": stages,
                 "stages_sum_ms": float(st.sum()) + stages["set_measurements_and_host"],
-                "solve_ms": solve, "launches_per_step": r["launches"] / len(ms)}
+                "solve_ms": solve, "launches_per_step": r["launches"] / len(ms),
+                "flat_fallbacks_per_step": r["restarted"] / len(ms)}
 
     sums = {name: summary(name) for name in legs}
     # headline: the faster start with device-resident inputs
@@ -718,7 +737,9 @@ def run_reference(args, dist):
 
 
 def main():
+    global MAX_ITER
     args = parse()
+    MAX_ITER = args.max_iter
     dist = Dist(args.gpus)
     if args.impl == "reference":
         out = run_reference(args, dist)

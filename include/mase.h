@@ -72,7 +72,9 @@ extern "C" {
 #define MASE_START_FLAT     0   /* Vm = 1, Va = 0                               */
 #define MASE_START_X0       1   /* x0 given to mase_solve                        */
 #define MASE_START_LEARNED  2   /* per-area MLP proposal (mase_warmstart_*),
-                                   kept only where it lowers J below the flat start */
+                                   kept only where it lowers J below the flat start;
+                                   a snapshot whose factor then breaks down is
+                                   solved again from the flat start           */
 /* schedule modes */
 #define MASE_PER_AREA   0   /* one launch per area and stage, like per-area streams */
 #define MASE_BATCHED    1   /* one launch per stage over every (area, snapshot)   */
@@ -146,7 +148,8 @@ typedef struct {
     double  *J;           /* r^T W r at the returned state, per snapshot        */
     double  *max_step;    /* max |dx| of the last step, per snapshot            */
     double   stage_ms[7]; /* where solve_ms went, in ms: [0] area kernel (evaluation,
-                             accumulation, condensation), [1] coordinator, [2] back-
+                             accumulation, condensation; with inner_iters also the
+                             inner steps' interior recoveries), [1] coordinator, [2] back-
                              substitution, [3] bookkeeping, each summed over the steps
                              from device clocks (first block start to last block end
                              of the stage's launches), or from CUDA events around the
@@ -158,7 +161,12 @@ typedef struct {
                              The seven sum to solve_ms.                           */
     double   solve_ms;       /* wall time of the solve on the library's stream    */
     int32_t  total_launches; /* kernels launched by the solve                   */
-    int32_t  steps;          /* Gauss-Newton steps run for the batch (max over snapshots) */
+    int32_t  steps;          /* Gauss-Newton steps run for the batch (max over snapshots),
+                                the flat-start fallback's included              */
+    int32_t  restarted;      /* snapshots of a learned start whose factor broke down
+                                from the networks' proposal (non-positive pivot or
+                                non-finite step) and were solved again from the flat
+                                start; their iters include the failed attempt's */
 } mase_stats;
 
 /* Structural sizes of a handle (host-side setup results). */
@@ -311,10 +319,17 @@ void mase_warmstart_default_options(mase_warmstart_options *opt);
 
 /* Train the per-area networks on n samples: z[n][m] measurements (canonical
  * order) and x[n][2N] states the estimator produced for them; both host or
- * both device pointers.  final_loss (may be NULL) receives the mean
- * normalised MSE per area over the last epoch.  Replaces any earlier model. */
-int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32_t n,
-                         const mase_warmstart_options *opt, double *final_loss);
+ * both device pointers.  mask[n][m] (1 = present, canonical order, the same
+ * memory kind as z; NULL = every row present) marks rows absent from a
+ * sample: an absent row enters neither the normalisation moments nor the
+ * sample's features (it reads as the row's mean, as at inference), and the
+ * magnitude skip of an absent voltage row falls back to that mean, so that
+ * networks trained on masked samples see what they will see under the same
+ * kind of drops.  final_loss (may be NULL) receives the mean normalised MSE
+ * per area over the last epoch.  Replaces any earlier model.  MASE_EINVAL for
+ * bad sizes or options, or for pointers of mixed memory kinds. */
+int mase_warmstart_train(mase_handle *h, const double *z, const uint8_t *mask, const double *x,
+                         int32_t n, const mase_warmstart_options *opt, double *final_loss);
 
 /* The networks' proposal x_out[n_snap][2N] for the handle's current
  * measurements (slack angle 0), without Gauss-Newton.  x_out host or device. */

@@ -60,6 +60,8 @@ void destroy_warmstart(WarmStart *w);
 // and keeps, per snapshot, whichever of the learned and the flat start has
 // the lower objective.  Returns a MASE_* code.
 int learned_start(mase_handle *h, int *launches);
+// per snapshot, 1 where the last learned start kept the networks' proposal
+const int *learned_picked(const mase_handle *h);
 // Adds r^T W r at the states (xV, xT) to J[s] for every snapshot (area kernel
 // in objective mode); J must be zeroed by the caller.
 void launch_objective(mase_handle *h, double *xV, double *xT, double *J, int *launches);
@@ -121,6 +123,7 @@ struct mase_handle {
     DevBuf<int> active, err, iters, status, n_active;
     DevBuf<unsigned long long> maxstep;
     int *h_n_active = nullptr;   // pinned
+    DevBuf<int> restart;         // [S] snapshots of a flat-start fallback
     size_t smem_local = 0, smem_back = 0, smem_bnd = 0, smem_obj = 0;
     // launch configuration (autotuned at create when options.autotune)
     std::vector<std::unique_ptr<LocalClass>> lcls;   // area-kernel launch classes

@@ -1219,6 +1219,8 @@ __global__ void __launch_bounds__(512) k_back(const AreaDev *__restrict__ areas,
 // this header without MASE_SHARED_TEMPLATES_ONLY)
 __global__ void k_gather_rows(const double *__restrict__ src, double *__restrict__ dst,
                               const int *__restrict__ perm, int M, int S);
+__global__ void k_gather_mask(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                              const int *__restrict__ perm, int M, int S);
 __global__ void k_state_in(const double *__restrict__ x, double *xV, double *xT,
                            const int *__restrict__ bus_of_ibus, int N, int S, int flat);
 __global__ void k_state_out(double *__restrict__ x, const double *xV, const double *xT,
@@ -1370,6 +1372,31 @@ __global__ void k_reset(State X, int *iters, int *status, double *laststep, Step
         iters[s] = 0;
         status[s] = 1;
         laststep[s] = 0.0;
+    }
+}
+
+// Flat-start fallback of the learned start: every snapshot flagged in
+// `restart` goes back to Vm = 1, Va = 0 with a fresh iteration count and is
+// the only kind left active; the step counter of the loop starts again.
+__global__ void k_restart(State X, int *iters, int *status, double *laststep, const int *restart,
+                          StepCtl ctl) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ctl.steps = 0;
+    const long long n = (long long)X.N * X.S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / X.N;
+        if (!restart[s]) continue;
+        X.xV[i] = 1.0;
+        X.xT[i] = 0.0;
+        if (i - s * X.N == 0) {
+            X.active[s] = 1;
+            X.err[s] = 0;
+            X.J[s] = 0.0;
+            X.maxstep[s] = 0ull;
+            iters[s] = 0;
+            status[s] = 1;
+            laststep[s] = 0.0;
+        }
     }
 }
 

@@ -235,10 +235,12 @@ int enqueue_step(mase_handle *h, int *launches) {
     Xc.clk = h->clk.p + 2;
     Xb.clk = h->clk.p + 4;
     // local Gauss-Newton steps with the boundary held fixed (Eq. local_wls):
-    // the area pass, then the interior recovery with a zero boundary step
+    // the area pass, then the interior recovery with a zero boundary step.
+    // Both count towards the area stage's clock, so that the stages' spans
+    // within a step stay disjoint.
     for (int q = 0; q < h->opt.inner_iters; ++q) {
         launch_local<RG, RS>(h, Xa, fac, cv, launches);
-        launch_back<RG, RS>(h, Xb, fac, cv, h->dx_zero.p, launches);
+        launch_back<RG, RS>(h, Xa, fac, cv, h->dx_zero.p, launches);
     }
     if (h->opt.inner_iters > 0) {
         // the outer step alone decides convergence
@@ -827,13 +829,15 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     CK(cudaEventRecord(ev[3], st));
     const bool device_loop = h->opt.use_graph && !h->opt.profile;
     double ev_acc[4] = {0, 0, 0, 0};
-    if (device_loop) {
-        if (!h->graph_exec) {
-            int rc = build_loop_graph<RG, RS>(h);
-            if (rc != MASE_OK) return rc;
+    auto run_loop = [&]() -> int {
+        if (device_loop) {
+            if (!h->graph_exec) {
+                int rc = build_loop_graph<RG, RS>(h);
+                if (rc != MASE_OK) return rc;
+            }
+            CK(cudaGraphLaunch(h->graph_exec, st));
+            return MASE_OK;
         }
-        CK(cudaGraphLaunch(h->graph_exec, st));
-    } else {
         for (int it = 0; it < max_iter; ++it) {
             int rc = enqueue_step<RG, RS>(h, &launches);
             if (rc != MASE_OK) return rc;
@@ -850,34 +854,77 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
             }
             if (*h->h_n_active == 0) break;
         }
-    }
-    CK(cudaEventRecord(ev[4], st));
-    int rc = enqueue_objective(h, &launches);
-    if (rc != MASE_OK) return rc;
-    if (x_out) {
-        if (is_device_ptr(x_out)) {
-            k_state_out<<<1024, 256, 0, st>>>(x_out, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
-        } else {
-            k_state_out<<<1024, 256, 0, st>>>(h->xbuf.p, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
-            CK(cudaMemcpyAsync(x_out, h->xbuf.p, (size_t)2 * N * nS * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-        }
-        ++launches;
-    }
-    std::vector<int> iters(nS), status(nS);
+        return MASE_OK;
+    };
+    std::vector<int> iters(nS), status(nS), picked(nS, 0);
     std::vector<double> J(nS), last(nS);
     double acc[4] = {0, 0, 0, 0};
     int steps = 0;
-    CK(cudaMemcpyAsync(iters.data(), h->iters.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(status.data(), h->status.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(J.data(), h->J.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(last.data(), h->laststep.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(acc, h->clk_acc.p, sizeof(acc), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&steps, h->steps_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaEventRecord(ev[5], st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
-    if (device_loop) launches += h->graph_launches * steps;
+    // objective at the final states, the states out and the per-snapshot results
+    auto finish = [&]() -> int {
+        CK(cudaEventRecord(ev[4], st));
+        int rc = enqueue_objective(h, &launches);
+        if (rc != MASE_OK) return rc;
+        if (x_out) {
+            if (is_device_ptr(x_out)) {
+                k_state_out<<<1024, 256, 0, st>>>(x_out, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
+            } else {
+                k_state_out<<<1024, 256, 0, st>>>(h->xbuf.p, h->xV.p, h->xT.p, h->bus_of_ibus.p, N, nS);
+                CK(cudaMemcpyAsync(x_out, h->xbuf.p, (size_t)2 * N * nS * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+            }
+            ++launches;
+        }
+        int steps_now = 0;
+        CK(cudaMemcpyAsync(iters.data(), h->iters.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(status.data(), h->status.p, nS * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(J.data(), h->J.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(last.data(), h->laststep.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(acc, h->clk_acc.p, sizeof(acc), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&steps_now, h->steps_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (learned)
+            CK(cudaMemcpyAsync(picked.data(), mase_internal::learned_picked(h), nS * sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(ev[5], st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        steps += steps_now;
+        if (device_loop) launches += h->graph_launches * steps_now;
+        return MASE_OK;
+    };
+    int n_restarted = 0;
+    int rc = run_loop();
+    if (rc != MASE_OK) return rc;
+    rc = finish();
+    if (rc != MASE_OK) return rc;
+    // flat-start fallback: a snapshot that started from the networks'
+    // proposal and whose factor broke down (non-positive pivot or non-finite
+    // step) is solved again from the flat start; its iteration count keeps
+    // the steps spent on the failed attempt
+    if (learned) {
+        std::vector<int> again(nS, 0), spent(nS, 0);
+        int n_again = 0;
+        for (int s = 0; s < nS; ++s)
+            if (picked[s] && (status[s] == MASE_SNAP_NOT_SPD || status[s] == MASE_SNAP_NONFINITE)) {
+                again[s] = 1;
+                spent[s] = iters[s];
+                ++n_again;
+            }
+        if (n_again) {
+            if (!h->restart.p) CK(h->restart.alloc(nS));
+            CK(cudaMemcpyAsync(h->restart.p, again.data(), nS * sizeof(int), cudaMemcpyHostToDevice, st));
+            k_restart<<<1024, 256, 0, st>>>(X, h->iters.p, h->status.p, h->laststep.p, h->restart.p,
+                                            make_ctl(h));
+            ++launches;
+            CK(cudaGetLastError());
+            rc = run_loop();
+            if (rc != MASE_OK) return rc;
+            rc = finish();
+            if (rc != MASE_OK) return rc;
+            for (int s = 0; s < nS; ++s) iters[s] += spent[s];
+        }
+        n_restarted = n_again;
+    }
     if (h->opt.profile)
         for (int i = 0; i < 4; ++i) acc[i] = ev_acc[i];
     int ret = MASE_OK;
@@ -896,6 +943,7 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         }
         stats->total_launches = launches;
         stats->steps = steps;
+        stats->restarted = n_restarted;
         float t_all = 0.f, t_pre = 0.f, t_ws = 0.f, t_stop = 0.f, t_loop = 0.f, t_post = 0.f;
         CK(cudaEventElapsedTime(&t_all, ev[0], ev[5]));
         CK(cudaEventElapsedTime(&t_pre, ev[0], ev[1]));

@@ -200,21 +200,25 @@ __global__ void k_features(const double *__restrict__ z, long long zstride, cons
     }
 }
 
-// per-slot statistics over samples (FP64 sums): feature slots read z rows,
-// output slots read the state
-__global__ void k_moments_rows(const double *__restrict__ z, long long zstride, const int *src,
-                               int FS, int S, double *sum, double *sum2) {
+// per-slot statistics over samples (FP64 sums): feature slots read the z
+// rows present in the sample (all rows without a mask), output slots read
+// the state
+__global__ void k_moments_rows(const double *__restrict__ z, long long zstride, const uint8_t *mask,
+                               const int *src, int FS, int S, double *sum, double *sum2, double *cnt) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < FS; f += gridDim.x * blockDim.x) {
         const int r = src[f];
         if (r < 0) continue;
-        double a = 0, b = 0;
+        double a = 0, b = 0, c = 0;
         for (int s = 0; s < S; ++s) {
+            if (mask && !mask[(long long)s * zstride + r]) continue;
             const double v = z[(long long)s * zstride + r];
             a += v;
             b += v * v;
+            c += 1.0;
         }
         sum[f] += a;
         sum2[f] += b;
+        cnt[f] += c;
     }
 }
 
@@ -234,13 +238,15 @@ __device__ __forceinline__ double skip_value(const double *z, long long zstride,
 }
 __global__ void k_moments_out(const double *__restrict__ xV, const double *__restrict__ xT, int N,
                               const int *dst, const int *skip, const double *__restrict__ z,
-                              long long zstride, int OS, int S, double *sum, double *sum2) {
+                              long long zstride, const uint8_t *mask, const float *skip_mu, int OS,
+                              int S, double *sum, double *sum2) {
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < OS; o += gridDim.x * blockDim.x) {
         const int code = dst[o];
         if (code < 0) continue;
         double a = 0, b = 0;
         for (int s = 0; s < S; ++s) {
-            const double v = state_at(xV, xT, s, N, code) - skip_value(z, zstride, nullptr, s, skip[o], 0.0);
+            const double v = state_at(xV, xT, s, N, code) -
+                             skip_value(z, zstride, mask, s, skip[o], (double)skip_mu[o]);
             a += v;
             b += v * v;
         }
@@ -250,7 +256,8 @@ __global__ void k_moments_out(const double *__restrict__ xV, const double *__res
 }
 __global__ void k_targets(const double *__restrict__ xV, const double *__restrict__ xT, int N,
                           const int *dst, const int *skip, const double *__restrict__ z,
-                          long long zstride, const float *mu, const float *sd, int OS, int S, float *T) {
+                          long long zstride, const uint8_t *mask, const float *skip_mu,
+                          const float *mu, const float *sd, int OS, int S, float *T) {
     const long long n = (long long)S * OS;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -261,13 +268,15 @@ __global__ void k_targets(const double *__restrict__ xV, const double *__restric
             T[i] = 0.f;
             continue;
         }
-        const double v = state_at(xV, xT, s, N, code) - skip_value(z, zstride, nullptr, s, skip[o], 0.0);
+        const double v = state_at(xV, xT, s, N, code) -
+                         skip_value(z, zstride, mask, s, skip[o], (double)skip_mu[o]);
         T[i] = (float)((v - (double)mu[o]) / (double)sd[o]);
     }
 }
-__global__ void k_finish_moments(const double *sum, const double *sum2, double n, int F, float *mu,
-                                 float *sd) {
+__global__ void k_finish_moments(const double *sum, const double *sum2, const double *cnt, double n,
+                                 int F, float *mu, float *sd) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+        if (cnt) n = fmax(cnt[f], 1.0);   // samples in which the row was present
         const double m = sum[f] / n;
         const double var = fmax(sum2[f] / n - m * m, 0.0);
         mu[f] = (float)m;
@@ -758,18 +767,23 @@ void backward(mase_handle *h, WarmStart &W, Workspace &ws) {
 }
 
 // moments and normalised features/targets of a chunk of internal-layout data
-int ingest_chunk(mase_handle *h, const double *z_can, const double *x_can, int n,
-                 bool host, DevBuf<double> &zc, DevBuf<double> &zi, DevBuf<double> &xc,
-                 DevBuf<double> &xv, DevBuf<double> &xt) {
+int ingest_chunk(mase_handle *h, const double *z_can, const uint8_t *mask_can, const double *x_can,
+                 int n, bool host, DevBuf<double> &zc, DevBuf<double> &zi, DevBuf<uint8_t> &mc,
+                 DevBuf<uint8_t> &mi, DevBuf<double> &xc, DevBuf<double> &xv, DevBuf<double> &xt) {
     cudaStream_t st = h->stream;
     const int M = h->S.m, N = h->S.N;
     const double *zsrc = z_can, *xsrc = x_can;
+    const uint8_t *msrc = mask_can;
     if (host) {
         WK(cudaMemcpyAsync(zc.p, z_can, (size_t)n * M * sizeof(double), cudaMemcpyHostToDevice, st));
         WK(cudaMemcpyAsync(xc.p, x_can, (size_t)n * 2 * N * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (mask_can)
+            WK(cudaMemcpyAsync(mc.p, mask_can, (size_t)n * M, cudaMemcpyHostToDevice, st));
         zsrc = zc.p;
         xsrc = xc.p;
+        msrc = mc.p;
     }
+    if (mask_can) mase_dev::k_gather_mask<<<1024, 256, 0, st>>>(msrc, mi.p, h->zperm.p, M, n);
     mase_dev::k_gather_rows<<<1024, 256, 0, st>>>(zsrc, zi.p, h->zperm.p, M, n);
     mase_dev::k_state_in<<<1024, 256, 0, st>>>(xsrc, xv.p, xt.p, h->bus_of_ibus.p, N, n, 0);
     WK(cudaGetLastError());
@@ -777,6 +791,8 @@ int ingest_chunk(mase_handle *h, const double *z_can, const double *x_can, int n
 }
 
 }  // namespace
+
+const int *learned_picked(const mase_handle *h) { return h->ws ? h->ws->picked.p : nullptr; }
 
 // learned start for the handle's current batch, judged against the flat start
 int learned_start(mase_handle *h, int *launches) {
@@ -839,8 +855,8 @@ void mase_warmstart_default_options(mase_warmstart_options *o) {
     o->seed = 1;
 }
 
-int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32_t n,
-                         const mase_warmstart_options *opt_in, double *final_loss) {
+int mase_warmstart_train(mase_handle *h, const double *z, const uint8_t *mask, const double *x,
+                         int32_t n, const mase_warmstart_options *opt_in, double *final_loss) {
     if (!h || !z || !x) return fail(MASE_EINVAL, "null argument");
     mase_warmstart_options opt;
     if (opt_in) opt = *opt_in;
@@ -866,50 +882,73 @@ int mase_warmstart_train(mase_handle *h, const double *z, const double *x, int32
     const bool zh = !is_device_pointer(z), xh = !is_device_pointer(x);
     const bool host = zh || xh;
     if (zh != xh) return fail(MASE_EINVAL, "z and x must both be host or both device pointers");
-    // pass 1: moments of features and targets; pass 2: normalised training set
+    if (mask && is_device_pointer(mask) == host)
+        return fail(MASE_EINVAL, "mask must be a host pointer exactly when z and x are");
+    // pass 1: moments of the features (over the samples in which each row is
+    // present); pass 2: moments of the targets, whose magnitude skip falls
+    // back to the feature mean where its row is absent; pass 3: normalised
+    // training set
     const int chunk = 512;
-    DevBuf<double> zc, zi, xc, xv, xt, fs1, fs2, os1, os2;
+    DevBuf<double> zc, zi, xc, xv, xt, fs1, fs2, fcnt, os1, os2;
+    DevBuf<uint8_t> mc, mi;
     WK(zi.alloc((size_t)chunk * M));
     WK(xv.alloc((size_t)chunk * N));
     WK(xt.alloc((size_t)chunk * N));
     if (host) {
         WK(zc.alloc((size_t)chunk * M));
         WK(xc.alloc((size_t)chunk * 2 * N));
+        if (mask) WK(mc.alloc((size_t)chunk * M));
     }
+    if (mask) WK(mi.alloc((size_t)chunk * M));
+    const uint8_t *mchunk = mask ? mi.p : nullptr;
     WK(fs1.alloc(W->FS));
     WK(fs2.alloc(W->FS));
+    WK(fcnt.alloc(W->FS));
     WK(os1.alloc(W->OS));
     WK(os2.alloc(W->OS));
     WK(cudaMemsetAsync(fs1.p, 0, W->FS * sizeof(double), st));
     WK(cudaMemsetAsync(fs2.p, 0, W->FS * sizeof(double), st));
+    WK(cudaMemsetAsync(fcnt.p, 0, W->FS * sizeof(double), st));
     WK(cudaMemsetAsync(os1.p, 0, W->OS * sizeof(double), st));
     WK(cudaMemsetAsync(os2.p, 0, W->OS * sizeof(double), st));
+    auto ingest = [&](int s0, int c) {
+        return ingest_chunk(h, z + (size_t)s0 * M, mask ? mask + (size_t)s0 * M : nullptr,
+                            x + (size_t)s0 * 2 * N, c, host, zc, zi, mc, mi, xc, xv, xt);
+    };
     for (int s0 = 0; s0 < n; s0 += chunk) {
         const int c = std::min(chunk, n - s0);
-        rc = ingest_chunk(h, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        rc = ingest(s0, c);
         if (rc != MASE_OK) return rc;
-        k_moments_rows<<<grid_for(W->FS), 256, 0, st>>>(zi.p, M, W->feat_src.p, W->FS, c, fs1.p, fs2.p);
-        k_moments_out<<<grid_for(W->OS), 256, 0, st>>>(xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M,
-                                                      W->OS, c, os1.p, os2.p);
+        k_moments_rows<<<grid_for(W->FS), 256, 0, st>>>(zi.p, M, mchunk, W->feat_src.p, W->FS, c, fs1.p,
+                                                       fs2.p, fcnt.p);
     }
-    k_finish_moments<<<grid_for(W->FS), 256, 0, st>>>(fs1.p, fs2.p, (double)n, W->FS, W->feat_mu.p, W->feat_sd.p);
-    k_finish_moments<<<grid_for(W->OS), 256, 0, st>>>(os1.p, os2.p, (double)n, W->OS, W->out_mu.p, W->out_sd.p);
+    k_finish_moments<<<grid_for(W->FS), 256, 0, st>>>(fs1.p, fs2.p, fcnt.p, (double)n, W->FS, W->feat_mu.p,
+                                                     W->feat_sd.p);
     rc = set_skip_means(h, *W);
     if (rc != MASE_OK) return rc;
+    for (int s0 = 0; s0 < n; s0 += chunk) {
+        const int c = std::min(chunk, n - s0);
+        rc = ingest(s0, c);
+        if (rc != MASE_OK) return rc;
+        k_moments_out<<<grid_for(W->OS), 256, 0, st>>>(xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M,
+                                                      mchunk, W->skip_mu.p, W->OS, c, os1.p, os2.p);
+    }
+    k_finish_moments<<<grid_for(W->OS), 256, 0, st>>>(os1.p, os2.p, nullptr, (double)n, W->OS, W->out_mu.p,
+                                                     W->out_sd.p);
     DevBuf<bf16> Xall;
     DevBuf<float> Tall;
     WK(Xall.alloc((size_t)n * W->FS));
     WK(Tall.alloc((size_t)n * W->OS));
     for (int s0 = 0; s0 < n; s0 += chunk) {
         const int c = std::min(chunk, n - s0);
-        rc = ingest_chunk(h, z + (size_t)s0 * M, x + (size_t)s0 * 2 * N, c, host, zc, zi, xc, xv, xt);
+        rc = ingest(s0, c);
         if (rc != MASE_OK) return rc;
         k_features<<<grid_for((long long)c * W->FS), 256, 0, st>>>(
-            zi.p, M, nullptr, W->feat_src.p, W->feat_mu.p, W->feat_sd.p, W->FS, c,
+            zi.p, M, mchunk, W->feat_src.p, W->feat_mu.p, W->feat_sd.p, W->FS, c,
             Xall.p + (size_t)s0 * W->FS);
         k_targets<<<grid_for((long long)c * W->OS), 256, 0, st>>>(
-            xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M, W->out_mu.p, W->out_sd.p, W->OS, c,
-            Tall.p + (size_t)s0 * W->OS);
+            xv.p, xt.p, N, W->out_dst.p, W->out_skip.p, zi.p, M, mchunk, W->skip_mu.p, W->out_mu.p,
+            W->out_sd.p, W->OS, c, Tall.p + (size_t)s0 * W->OS);
     }
     WK(cudaGetLastError());
     // training

@@ -51,7 +51,7 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", _i32p), ("status", _i32p), ("J", _f64p), ("max_step", _f64p),
                 ("stage_ms", C.c_double * 7), ("solve_ms", C.c_double), ("total_launches", C.c_int32),
-                ("steps", C.c_int32)]
+                ("steps", C.c_int32), ("restarted", C.c_int32)]
 
 
 class WarmstartOptions(C.Structure):
@@ -120,7 +120,7 @@ def load() -> C.CDLL:
         "mase_coordinator_noalloc": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                                C.c_void_p, C.c_int64]),
         "mase_warmstart_default_options": (None, [C.POINTER(WarmstartOptions)]),
-        "mase_warmstart_train": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int32,
+        "mase_warmstart_train": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                            C.POINTER(WarmstartOptions), C.POINTER(C.c_double)]),
         "mase_warmstart_predict": (C.c_int, [H, C.c_void_p]),
         "mase_warmstart_save": (C.c_int, [H, C.c_char_p]),
@@ -254,6 +254,7 @@ class SolveResult:
     steps: int
     stage_ms: tuple     # area, coordinator, back, bookkeeping, learned start, start/finish, loop gaps
     solve_ms: float
+    restarted: int = 0  # learned-start snapshots solved again from the flat start
 
 
 class Estimator:
@@ -319,7 +320,7 @@ class Estimator:
         if check and rc < 0:
             raise MaseError(rc, _last_error())
         return SolveResult(rc, iters, status, J, ms, int(st.total_launches), int(st.steps),
-                           tuple(st.stage_ms), float(st.solve_ms))
+                           tuple(st.stage_ms), float(st.solve_ms), int(st.restarted))
 
     def measure(self, x, z_out, n_snap=None):
         n = self.n_snap if n_snap is None else n_snap
@@ -341,14 +342,20 @@ class Estimator:
 
     # ---- learned warm start
     def warmstart_train(self, z, x, epochs=20, batch=256, lr=1e-3, weight_decay=1e-4, hidden=512,
-                        seed=1) -> float:
-        """Train the per-area networks on (z, x) pairs; returns the last-epoch loss."""
+                        seed=1, mask=None) -> float:
+        """Train the per-area networks on (z, x) pairs, with an optional
+        presence mask [n][m] (uint8, 1 = present) per sample; returns the
+        last-epoch loss."""
+        if mask is not None:
+            if tuple(mask.shape) != tuple(z.shape) or "uint8" not in str(mask.dtype):
+                raise ValueError("mask must be uint8 with the shape of z")
         o = WarmstartOptions()
         self.lib.mase_warmstart_default_options(C.byref(o))
         o.hidden, o.epochs, o.batch, o.lr, o.weight_decay, o.seed = hidden, epochs, batch, lr, weight_decay, seed
         loss = C.c_double()
         n = int(z.shape[0])
-        rc = self.lib.mase_warmstart_train(self.h, _ptr(z), _ptr(x), n, C.byref(o), C.byref(loss))
+        rc = self.lib.mase_warmstart_train(self.h, _ptr(z), _ptr(mask), _ptr(x), n, C.byref(o),
+                                           C.byref(loss))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
         return loss.value

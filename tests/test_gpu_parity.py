@@ -239,19 +239,19 @@ def test_stage_times_account_for_the_solve(mase):
     per-step round trips."""
     g = synth.make_grid("grid2869_k16")
     net, Vm, Va, z, sig = problem(g, 8, 4100)
-    for use_graph in (True, False):
+    for use_graph, inner in ((True, 0), (False, 0), (True, 2)):
         est = mase.Estimator(g, sig, 8, z=z, precision=mase.MIXED, schedule=mase.BATCHED,
-                             use_graph=use_graph)
+                             use_graph=use_graph, inner_iters=inner)
         est.solve(tol=1e-8, max_iter=10)
         r = est.solve(tol=1e-8, max_iter=10)
         est.close()
         st = np.array(r.stage_ms)
         assert r.rc == mase.MASE_OK and r.steps == int(r.iters.max())
-        assert np.all(st[:6] >= 0.0) and st[6] >= -0.01, st
+        assert np.all(st[:6] >= 0.0) and st[6] >= -0.01, (inner, st)
         assert st[0] > 0 and st[1] > 0 and st[2] > 0 and st[3] > 0
         assert abs(st.sum() - r.solve_ms) <= 1e-3 * r.solve_ms + 1e-3, (st, r.solve_ms)
         if use_graph:
-            assert st[6] <= 0.2 * r.solve_ms, st
+            assert st[6] <= 0.2 * r.solve_ms, (inner, st)
 
 
 def test_bounded_wait_gives_up_with_device_status(mase):

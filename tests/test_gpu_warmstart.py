@@ -169,6 +169,114 @@ def test_learned_start_gain_and_parity(mase):
     est.close()
 
 
+def test_learned_start_trained_under_drops(mase):
+    """Networks trained on masked samples (10 % of rows dropped at random per
+    sample, the training snapshots solved under their masks) still cut
+    Gauss-Newton steps on a held-out walk with fresh random drops, and the
+    estimates stay the oracle's for the masked problem."""
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    N, S = g.n_bus, 64
+    sig = synth.sigma_vector(g.n_bus, g.n_branch)
+    est = mase.Estimator(g, sig, S, z=None, precision=mase.MIXED, schedule=mase.BATCHED)
+    masks = [torch.tensor(synth.make_mask(g, S, 0.10, 21000 + b), device="cuda") for b in range(4)]
+    Z, X, Ms = [], [], []
+    for b in range(128):                      # 8192 independent training states
+        z = _batch(mase, est, g, 20000 + 7 * b, S, walk=1)
+        est.set_measurements(z, masks[b % 4])
+        x = torch.zeros((S, 2 * N), dtype=torch.float64, device="cuda")
+        r = est.solve(tol=1e-8, max_iter=10, x_out=x, check=False)
+        ok = torch.tensor(r.status == 0, device="cuda")
+        Z.append(z[ok])
+        X.append(x[ok])
+        Ms.append(masks[b % 4][ok])
+    with pytest.raises(ValueError):
+        est.warmstart_train(torch.cat(Z), torch.cat(X), mask=torch.cat(Ms)[:-1])
+    est.warmstart_train(torch.cat(Z), torch.cat(X), epochs=30, batch=256, lr=1e-3, mask=torch.cat(Ms))
+    net, Vm, Va, zh, _ = problem(g, S, 4343)
+    mh = synth.make_mask(g, S, 0.10, 4344)
+    est.set_measurements(torch.tensor(zh, device="cuda"), torch.tensor(mh, device="cuda"))
+    xf = np.zeros((S, 2 * N))
+    rf = est.solve(tol=1e-8, max_iter=15, x_out=xf)
+    est.set_start_mode(mase.START_LEARNED)
+    xl = np.zeros((S, 2 * N))
+    rl = est.solve(tol=1e-8, max_iter=15, x_out=xl)
+    assert np.all(rl.status == 0) and np.all(rf.status == 0)
+    assert rl.iters.mean() < rf.iters.mean(), (rl.iters.mean(), rf.iters.mean())
+    for s in (0, 40):
+        ref = wls.gauss_newton(net, zh[s], wls.weights(sig, mh[s]), tol=1e-8, max_iter=30)
+        assert np.max(np.abs(xl[s, :N] - ref.Vm)) <= 1e-6
+        assert np.max(np.abs(xl[s, N:] - ref.Va)) <= 1e-6
+    est.close()
+
+
+def _edit_model(path, **arrays):
+    """Rewrite named float arrays (fm, fsd, om, osd) of a saved warm-start file."""
+    raw = bytearray(open(path, "rb").read())
+    K, Hd, FS, OS = np.frombuffer(bytes(raw[8:24]), dtype=np.int32)
+    off = 24 + 8 * int(K) + 8
+    spans = {}
+    for name, n in (("fm", FS), ("fsd", FS), ("om", OS), ("osd", OS)):
+        spans[name] = (off, int(n))
+        off += 4 * int(n)
+    for name, fn in arrays.items():
+        o, n = spans[name]
+        v = np.frombuffer(bytes(raw[o:o + 4 * n]), dtype=np.float32).copy()
+        raw[o:o + 4 * n] = fn(v).astype(np.float32).tobytes()
+    open(path, "wb").write(bytes(raw))
+
+
+def test_learned_start_falls_back_to_flat(mase):
+    """A proposal that lowers J but leaves one bus at Vm = 0 (its angle column
+    of H is then exactly zero, so the factor meets a zero pivot) is solved
+    again from the flat start: every snapshot converges to the oracle's
+    estimate, and its iteration count includes the failed attempt."""
+    import torch
+    g = synth.make_grid("grid2869_k16")
+    N, S = g.n_bus, 16
+    net, Vm, Va, zh, sig = problem(g, S, 4400)
+    deg = np.bincount(np.concatenate([g.from_bus, g.to_bus]), minlength=N)
+    b = int(np.nonzero((deg >= 3) & (np.arange(N) != g.slack))[0][0])
+    mask = np.ones((S, g.n_meas), dtype=np.uint8)
+    mask[:, b] = 0                                   # the Vm row of bus b
+    for s in range(S):                               # the proposal below is kept
+        w = wls.weights(sig, mask[s])
+        vp = zh[s, :N].copy()
+        vp[b] = 0.0
+        assert wls.objective(net, zh[s], w, vp, np.zeros(N)) < \
+            wls.objective(net, zh[s], w, np.ones(N), np.zeros(N))
+    est = mase.Estimator(g, sig, S, z=torch.tensor(zh, device="cuda"),
+                         mask=torch.tensor(mask, device="cuda"), precision=mase.MIXED,
+                         schedule=mase.BATCHED)
+    xf = np.zeros((S, 2 * N))
+    rf = est.solve(tol=1e-8, max_iter=15, x_out=xf)
+    assert rf.restarted == 0
+    zt = torch.tensor(zh, device="cuda")
+    est.warmstart_train(zt, torch.tensor(xf, device="cuda"), epochs=1, batch=8, hidden=64)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ws.bin")
+        est.warmstart_save(path)
+        # outputs ignore the networks (zero output scale): magnitudes are the
+        # measured Vm (the skip row), angles 0; with zero feature means the
+        # absent Vm row of bus b reads as 0, so its proposal is Vm = 0
+        _edit_model(path, fm=lambda v: v * 0, om=lambda v: v * 0, osd=lambda v: v * 0)
+        est.warmstart_load(path)
+    xp = np.zeros((S, 2 * N))
+    est.warmstart_predict(xp)
+    assert np.all(xp[:, b] == 0.0) and np.all(xp[:, N:] == 0.0)
+    est.set_start_mode(mase.START_LEARNED)
+    xl = np.zeros((S, 2 * N))
+    rl = est.solve(tol=1e-8, max_iter=15, x_out=xl)
+    assert rl.restarted == S, rl.restarted
+    assert np.all(rl.status == 0)
+    assert np.all(rl.iters >= rf.iters + 1), (rl.iters, rf.iters)
+    for s in (0, 9):
+        ref = wls.gauss_newton(net, zh[s], wls.weights(sig, mask[s]), tol=1e-8, max_iter=30)
+        assert np.max(np.abs(xl[s, :N] - ref.Vm)) <= 1e-6
+        assert np.max(np.abs(xl[s, N:] - ref.Va)) <= 1e-6
+    est.close()
+
+
 def test_learned_start_requires_a_model(mase):
     g = synth.make_grid("grid300_k4")
     net, Vm, Va, z, sig = problem(g, 2, 4300)
