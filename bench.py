@@ -40,7 +40,7 @@ METRIC = "MASE solves/s, 9241-bus x64 snapshots, vs plain FP64 GPU path at 1e-6 
 UNIT = "solves/s"
 WORKLOAD = "grid9241_k32"
 N_SNAP = 64
-STATE_SEED, NOISE_SEED = 2002, 2003
+STATE_SEED, NOISE_SEED, MASK_SEED = 2002, 2003, 2004
 TOL, MAX_ITER = 1e-8, 10
 WORKLOAD_DESC = "9241-bus/16049-branch synthetic grid, 32 areas (150-450 buses), 64-snapshot random walk"
 STAGES = ("area", "coordinator", "back", "bookkeeping", "learned_start", "start_finish", "loop_gaps")
@@ -189,6 +189,16 @@ def workload_inputs(args):
     return g, Vm, Va, e, sig
 
 
+def workload_mask(args, g):
+    """Presence mask [S][m] of the workload's measurement rows, or None."""
+    from paper_2604_23175_gb300 import synth
+    if args.family:
+        return synth.family_mask(g, args.family, args.snapshots)
+    if args.drop > 0:
+        return synth.make_mask(g, args.snapshots, args.drop, MASK_SEED)
+    return None
+
+
 def gemm_rate(torch, dtype, n=4096, reps=5):
     """Measured dense GEMM rate (TFLOP/s) of cuBLAS in the given dtype."""
     a = torch.randn(n, n, device="cuda", dtype=dtype)
@@ -296,11 +306,8 @@ def run_ours(args, dist):
     est.measure(x_true, z_dev)
     z_dev += torch.tensor(e, device="cuda")
     z_host = z_dev.cpu().numpy().copy()
-    mask_dev, mask_pin, mask_h = None, None, None
-    if args.family:
-        mask_h = synth.family_mask(g, args.family, S)
-    elif args.drop > 0:
-        mask_h = synth.make_mask(g, S, args.drop, 2004)
+    mask_dev, mask_pin = None, None
+    mask_h = workload_mask(args, g)
     if mask_h is not None:
         mask_dev = torch.tensor(mask_h, device="cuda")
         mask_pin = torch.from_numpy(mask_h).pin_memory()
@@ -618,7 +625,8 @@ e = synth.make_noise(g, args.snapshots, %(nseed)d)
 sig = synth.sigma_vector(g.n_bus, g.n_branch)
 net = wls.Net(g.n_bus, g.from_bus.astype(np.int64), g.to_bus.astype(np.int64), g.r, g.x, g.b_charge, g.slack)
 snaps = %(snaps)r
-w = wls.weights(sig)
+mask = bench.workload_mask(args, g)
+w = {s: wls.weights(sig, None if mask is None else mask[s]) for s in snaps}
 z = {s: wls.measure(net, Vm[s], Va[s]) + e[s] for s in snaps}
 part = wls.partition(net, g.area_of_bus, g.n_area) if %(multi)r else None
 sys.stdout.write("ready\n"); sys.stdout.flush()
@@ -627,9 +635,9 @@ t = time.perf_counter()
 res = {}
 for s in snaps:
     if part is None:
-        r = wls.gauss_newton(net, z[s], w, tol=%(tol)r, max_iter=%(mi)d)
+        r = wls.gauss_newton(net, z[s], w[s], tol=%(tol)r, max_iter=%(mi)d)
     else:
-        r = wls.multi_area_gauss_newton(net, part, z[s], w, tol=%(tol)r, max_iter=%(mi)d)
+        r = wls.multi_area_gauss_newton(net, part, z[s], w[s], tol=%(tol)r, max_iter=%(mi)d)
     res[s] = r
 dt = time.perf_counter() - t
 np.save(sys.argv[1], np.stack([np.concatenate([res[s].Vm, res[s].Va]) for s in snaps]))
@@ -730,7 +738,7 @@ def run_reference(args, dist):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "n_snap_per_step": P, "tol": TOL, "max_iter": MAX_ITER},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": P, "kind": "oracle",
-                             "sample": f"first {P} of the 64 snapshots per step, centralised FP64 Gauss-Newton "
+                             "sample": f"first {P} of the {args.snapshots} snapshots per step, centralised FP64 Gauss-Newton "
                                        f"(SciPy sparse LU), one snapshot per worker process"},
             "host": hi,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -330,14 +330,16 @@ def rows_touching_bus(grid: Grid):
 def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
               min_present: int = 4) -> np.ndarray:
     """Presence mask [n_snap][m] (1 = present) dropping ``drop_frac`` of rows
-    per snapshot at random, under one metering rule: every branch keeps at
+    per snapshot at random, under two metering rules: every branch keeps at
     least one of its two active-power flow rows and one of its two reactive
-    flow rows.  The draw removes exactly round(drop_frac * m) rows subject to
-    that rule (a pair drawn whole has one row, chosen at random, put back and
-    replaced by a fresh draw).  Then every bus keeps at least one present
-    active-power row and one present reactive/voltage row touching it, and at
-    least ``min_present`` touching rows in all (dropped rows restored at
-    random); this restores a handful of rows per snapshot.
+    flow rows, and every bus with a single branch keeps its voltage-magnitude
+    row.  The draw removes exactly round(drop_frac * m) rows subject to those
+    rules (leaf magnitude rows are never drawn; a flow pair drawn whole has
+    one row, chosen at random, put back and replaced by a fresh draw).  Then
+    every bus keeps at least one present active-power row and one present
+    reactive/voltage row touching it, and at least ``min_present`` touching
+    rows in all (dropped rows restored at random); this restores a handful of
+    rows per snapshot.
 
     The branch rule keeps both halves of the decoupled problem topologically
     observable (each branch joins its ends through a flow row of each kind).
@@ -346,7 +348,12 @@ def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
     reactive flows: its magnitude is then fixed through the neighbour's
     reactive injection, a quadratic relation with two roots, and Gauss-Newton
     from flat start can walk to the spurious low-voltage root (a stationary
-    point far from the true state) even though the network is observable."""
+    point far from the true state) even though the network is observable.
+    The leaf rule: every power row is unchanged when a bus's magnitude
+    changes sign and its angle moves by pi, or its angle by 2 pi, so only
+    the magnitude row tells those states apart.  A leaf without it is held by
+    its one branch alone, and Gauss-Newton from the flat start was seen to
+    wander between such equivalent states for 15-17 steps."""
     import scipy.sparse as sp
     rng = np.random.Generator(np.random.PCG64(seed))
     N, L, m = grid.n_bus, grid.n_branch, grid.n_meas
@@ -355,6 +362,10 @@ def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
     for a0, b0 in ((base, base + 2 * L), (base + L, base + 3 * L)):
         partner[a0:a0 + L] = b0 + np.arange(L)
         partner[b0:b0 + L] = a0 + np.arange(L)
+    deg = np.bincount(np.concatenate([grid.from_bus, grid.to_bus]).astype(np.int64), minlength=N)
+    keep = np.zeros(m, dtype=bool)
+    keep[np.nonzero(deg == 1)[0]] = True     # magnitude rows of leaves (rows 0..N-1)
+    drawable = np.nonzero(~keep)[0]
     first = np.concatenate([base + np.arange(L), base + L + np.arange(L)])
     p_rows, q_rows = _rows_touching_bus_by_kind(grid)
     all_rows = [np.union1d(p, q) for p, q in zip(p_rows, q_rows)]
@@ -370,7 +381,7 @@ def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
     out = np.ones((n_snap, m), dtype=np.uint8)
     for s in range(n_snap):
         row = np.ones(m, dtype=np.uint8)
-        row[rng.choice(m, size=k, replace=False)] = 0
+        row[rng.choice(drawable, size=k, replace=False)] = 0
         for _ in range(64):
             both = first[(row[first] == 0) & (row[partner[first]] == 0)]
             if len(both) == 0:
@@ -378,7 +389,7 @@ def make_mask(grid: Grid, n_snap: int, drop_frac: float, seed: int,
             back = np.where(rng.random(len(both)) < 0.5, both, partner[both])
             row[back] = 1
             # a fresh row may be drawn only where its pair partner is present
-            free = np.nonzero((row == 1) & ((partner < 0) | (row[np.maximum(partner, 0)] == 1)))[0]
+            free = np.nonzero((row == 1) & ~keep & ((partner < 0) | (row[np.maximum(partner, 0)] == 1)))[0]
             row[rng.choice(free, size=len(back), replace=False)] = 0
         else:
             raise RuntimeError("branch metering rule not met")

@@ -53,3 +53,24 @@ def test_oracle_baseline_children_on_a_small_grid():
     assert x.shape == (2, 600) and wall > 0 and all(o["iters"][0] >= 2 for o in outs)
     wall2, outs2, x2 = bench.oracle_run(argv, [[0, 1]], multi=True)
     assert np.max(np.abs(x - x2)) < 1e-9
+
+
+def test_oracle_baseline_children_use_the_workload_mask():
+    """Under random drops the CPU baseline solves the masked problem: its
+    estimate equals the oracle's own solve with the same mask and differs
+    from the unmasked one."""
+    from oracle import wls
+    from tests.helpers import net_of
+    argv = ["--workload", "grid300_k4", "--snapshots", "3", "--drop", "0.2"]
+    _, _, x = bench.oracle_run(argv, [[1]])
+    args = bench.parse_from(argv)
+    g = bench.workload_grid(args)
+    _, Vm, Va, e, sig = bench.workload_inputs(args)
+    mask = bench.workload_mask(args, g)
+    assert mask is not None and mask.shape == (3, g.n_meas) and mask[1].mean() < 0.85
+    net = net_of(g)
+    z = wls.measure(net, Vm[1], Va[1]) + e[1]
+    ref = wls.gauss_newton(net, z, wls.weights(sig, mask[1]), tol=bench.TOL, max_iter=bench.MAX_ITER)
+    full = wls.gauss_newton(net, z, wls.weights(sig), tol=bench.TOL, max_iter=bench.MAX_ITER)
+    assert np.max(np.abs(x[0] - np.concatenate([ref.Vm, ref.Va]))) < 1e-12
+    assert np.max(np.abs(x[0] - np.concatenate([full.Vm, full.Va]))) > 1e-6

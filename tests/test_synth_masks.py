@@ -2,8 +2,8 @@
 35 % of the rows dropped at random, the oracle's Gauss-Newton converges on
 every snapshot within 10 steps (a repair that only counts rows per bus
 leaves snapshots that need 14 steps or do not converge in 15), the dropped
-fraction stays at its target, and no branch loses both flow rows of one
-kind."""
+fraction stays at its target, no branch loses both flow rows of one kind,
+and no leaf bus loses its magnitude row."""
 import numpy as np
 
 from oracle import wls
@@ -36,4 +36,6 @@ def test_masks_are_deterministic_and_keep_both_row_kinds():
         assert all(a[s][q].any() for q in q_rows)
         for o in (base, base + L):          # P flows, Q flows: from end | to end
             assert np.all(a[s][o:o + L] | a[s][o + 2 * L:o + 3 * L])
+        deg = np.bincount(np.concatenate([g.from_bus, g.to_bus]), minlength=N)
+        assert np.all(a[s][:N][deg == 1] == 1)   # leaves keep their magnitude row
         assert abs((1.0 - a[s].mean()) - 0.10) < 2e-4
