@@ -358,6 +358,109 @@ __device__ __forceinline__ void diag_block_any(RG *P, int w, int ld, RS *yc, boo
     else diag_block_wide<RG, RS>(P, w, ld, yc, do_factor, lane, err);
 }
 
+// ---------------------------------------------------------------------------
+// Register-staged variants for a factor spread over both blocks of a cluster.
+// There half of every panel lies in the other block's shared memory, whose
+// loads take hundreds of cycles; the substitution chains above would wait on
+// one such load per column.  Here each lane first loads its own row (or
+// column) of the block in one go, and the chains move values between lanes
+// with shuffles only.
+// ---------------------------------------------------------------------------
+// (FP32 factors only: an FP64 block of 32 x 32 does not fit the registers.)
+template <class ST>
+struct RemoteStore {
+    static constexpr bool value = false;
+};
+template <>
+struct RemoteStore<ClusterStore<float>> {
+    static constexpr bool value = true;
+};
+
+// panel_rows with the factored diagonal block held by rows in the lanes
+// (lane k: row k; 1/L_kk on its diagonal).  All lanes take part in the
+// shuffles; rows past the panel are computed on zeros and not stored.
+template <class RG, int WB>
+__device__ void panel_rows_reg(RG *P, int w, int ld, int r0, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int row = r0 + lane;
+    const bool mine = row < ld;
+    RG Lr[WB], x[WB];
+#pragma unroll
+    for (int c = 0; c < WB; ++c) {
+        Lr[c] = (c < w && lane < w && c <= lane) ? P[(size_t)c * ld + lane] : RG(0);
+        x[c] = (mine && c < w) ? P[(size_t)c * ld + row] : RG(0);
+    }
+#pragma unroll
+    for (int c = 0; c < WB; ++c) {
+        if (c < w) {
+            x[c] *= __shfl_sync(FULL, Lr[c], c);
+#pragma unroll
+            for (int c2 = c + 1; c2 < WB; ++c2) x[c2] -= x[c] * __shfl_sync(FULL, Lr[c], c2);
+        }
+    }
+    if (mine) {
+#pragma unroll
+        for (int c = 0; c < WB; ++c)
+            if (c < w) P[(size_t)c * ld + row] = x[c];
+    }
+}
+
+template <class RG>
+__device__ __forceinline__ void panel_rows_reg_any(RG *P, int w, int ld, int r0, int lane) {
+    if (w <= 8) panel_rows_reg<RG, 8>(P, w, ld, r0, lane);
+    else if (w <= 16) panel_rows_reg<RG, 16>(P, w, ld, r0, lane);
+    else panel_rows_reg<RG, 32>(P, w, ld, r0, lane);
+}
+
+// diag_block_wide with the solve of the rows H..w-1 against L11 and the
+// trailing update done on registers: L11's rows are reloaded by the lanes
+// that hold them, L21's rows stay in the lanes that computed them.
+template <class RG, class RS>
+__device__ void diag_block_wide_reg(RG *P, int w, int ld, RS *yc, int lane, int *err) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int H = 16;
+    diag_block<RG, RS, H>(P, H, ld, yc, true, lane, err);
+    __syncwarp();
+    const int r = H + lane;
+    const bool mine = lane < w - H;
+    RG Lr[H], x[H];
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+        Lr[c] = (lane < H && c <= lane) ? P[(size_t)c * ld + lane] : RG(0);
+        x[c] = mine ? P[(size_t)c * ld + r] : RG(0);
+    }
+    // L21 = A21 L11^-T
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+        x[c] *= __shfl_sync(FULL, Lr[c], c);
+#pragma unroll
+        for (int c2 = c + 1; c2 < H; ++c2) x[c2] -= x[c] * __shfl_sync(FULL, Lr[c], c2);
+    }
+    if (mine) {
+#pragma unroll
+        for (int c = 0; c < H; ++c) P[(size_t)c * ld + r] = x[c];
+    }
+    // A22 -= L21 L21^T (lower part): row H + j of L21 is lane j's x
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        if (j < w - H) {
+            RG v = RG(0);
+#pragma unroll
+            for (int k = 0; k < H; ++k) v += x[k] * __shfl_sync(FULL, x[k], j);
+            if (mine && j <= lane) P[(size_t)(H + j) * ld + r] -= v;
+        }
+    }
+    // rhs of the trailing rows: y2 -= L21 y1
+    if (mine) {
+        RS v = RS(0);
+#pragma unroll
+        for (int k = 0; k < H; ++k) v += RS(x[k]) * yc[k];
+        yc[r] -= v;
+    }
+    __syncwarp();
+    diag_block<RG, RS, H>(P + (size_t)H * ld + H, w - H, ld, yc + H, true, lane, err);
+}
+
 template <class RG>
 __device__ __forceinline__ void panel_rows_any(RG *P, int w, int ld, int r0, int lane) {
     if (w <= 2) panel_rows<RG, 2>(P, w, ld, r0, lane);
@@ -440,10 +543,22 @@ __device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, con
 // per lane) and no tile spills.
 template <class RG, class RS, class ST>
 __device__ __noinline__ void task_diag(const ST st, int off, int w, int ld, RS *yc, int *err) {
+    if constexpr (RemoteStore<ST>::value) {
+        if (w > 16 && w <= 32) {
+            diag_block_wide_reg<RG, RS>(st.at(off), w, ld, yc, threadIdx.x & 31, err);
+            return;
+        }
+    }
     diag_block_any<RG, RS>(st.at(off), w, ld, yc, true, threadIdx.x & 31, err);
 }
 template <class RG, class ST>
 __device__ __noinline__ void task_panel(const ST st, int off, int w, int ld, int r0) {
+    if constexpr (RemoteStore<ST>::value) {
+        if (w <= 32) {
+            panel_rows_reg_any<RG>(st.at(off), w, ld, r0, threadIdx.x & 31);
+            return;
+        }
+    }
     panel_rows_any<RG>(st.at(off), w, ld, r0, threadIdx.x & 31);
 }
 template <class RG, class RS, class ST>
@@ -626,6 +741,26 @@ __device__ __forceinline__ RS chunk_colsum(const RG *P, int w, int ld, int row, 
     return v[0];
 }
 
+// Backward substitution with one diagonal block of at most 32 columns on
+// registers (lane r loads column r of L; 1/L_cc on the diagonal).
+template <class RG, class RS>
+__device__ __forceinline__ void back_diag_reg(const RG *P, int w, int ld, RS *yc, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    RG col[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) col[c] = (lane < w && c >= lane && c < w) ? P[(size_t)lane * ld + c] : RG(0);
+    RS t = lane < w ? yc[lane] : RS(0);
+#pragma unroll
+    for (int c = 31; c >= 0; --c) {
+        if (c < w) {
+            const RS xc = __shfl_sync(FULL, t * RS(col[c]), c);
+            if (lane == c) t = xc;
+            else if (lane < c) t -= RS(col[c]) * xc;
+        }
+    }
+    if (lane < w) yc[lane] = t;
+}
+
 // Backward solve L^T x = y over the internal supernodes, top level first.
 // y[n_int..] must hold the (already known) boundary unknowns; on return
 // y[0..n_int) holds the interior solution (Eq. backsub).
@@ -659,6 +794,12 @@ __device__ void back_solve(const FacDev &F, const Tables &T, const ST &st, RS *y
             const int s = F.sn_base + sn_order[i];
             const int w = T.sn_w[s], ld = w + T.sn_nr[s], c0 = T.sn_c0[s];
             const RG *P = st.at(T.sn_off[s]);
+            if constexpr (RemoteStore<ST>::value) {
+                if (w <= 32) {
+                    back_diag_reg<RG, RS>(P, w, ld, y + c0, lane);
+                    continue;
+                }
+            }
             for (int kb = ((w - 1) / 32) * 32; kb >= 0; kb -= 32) {
                 const int r = kb + lane;
                 RS t = r < w ? y[c0 + r] : RS(0);
