@@ -69,6 +69,9 @@ def parse():
                     help="split the workload's network into this many areas with the partitioner")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER,
                     help="Gauss-Newton step cap per snapshot")
+    ap.add_argument("--tensor-units", type=int, default=-1,
+                    help="update units of panels at least this wide on the tensor cores (3xTF32); "
+                         "0 = none, -1 = the library default")
     ap.add_argument("--inner-iters", type=int, default=0,
                     help="local Gauss-Newton steps per area with the boundary fixed before each condensed step")
     return ap.parse_args()
@@ -302,7 +305,8 @@ def run_ours(args, dist):
     z_dev = torch.empty((S, g.n_meas), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     est = mase.Estimator(g, sig, S, z=None, precision=mase.MIXED, schedule=mase.BATCHED,
-                         use_graph=True, refine=1, device=dev, stream=stream, inner_iters=args.inner_iters)
+                         use_graph=True, refine=1, device=dev, stream=stream, inner_iters=args.inner_iters,
+                         tensor_units=args.tensor_units)
     est.measure(x_true, z_dev)
     z_dev += torch.tensor(e, device="cuda")
     z_host = z_dev.cpu().numpy().copy()
@@ -475,7 +479,7 @@ def run_ours(args, dist):
     # every launch works on all snapshots, 6 steps), for the rooflines
     prof = mase.Estimator(g, sig, S, z=z_dev, mask=mask_dev, precision=mase.MIXED,
                           schedule=mase.BATCHED, refine=1, device=dev, stream=stream, profile=True,
-                          inner_iters=args.inner_iters)
+                          inner_iters=args.inner_iters, tensor_units=args.tensor_units)
     pst, psteps, pact = np.zeros(7), 0, []
     for i in range(1 + 3):
         flush()
@@ -540,11 +544,13 @@ def run_ours(args, dist):
     cmp.close()
 
     variant = bool(args.workload != WORKLOAD or S != 64 or args.areas or args.family or args.drop
-                   or args.inner_iters)
+                   or args.inner_iters or args.tensor_units >= 0)
     desc = WORKLOAD_DESC if not variant else (
         f"{g.name} x{S} snapshots" + (f", {args.family} rows dropped" if args.family else "")
         + (f", {100 * args.drop:g}% rows dropped at random" if args.drop else "")
-        + (f", {args.inner_iters} inner local steps" if args.inner_iters else ""))
+        + (f", {args.inner_iters} inner local steps" if args.inner_iters else "")
+        + (f", tensor-core update units from panel width {args.tensor_units}"
+           if args.tensor_units > 0 else ""))
     # every kernel of the library launched inside the timed region (all legs)
     launches = sum(r["launches"] for r in rec.values())
     out = {

@@ -138,6 +138,12 @@ typedef struct {
                             shared memory they need and the block size of
                             each class, the back-substitution block size and
                             the coordinator's form; mase_info reports them   */
+    int32_t tensor_units;/* MASE_MIXED: factorisation update units whose source
+                            panel has at least this many columns run on the
+                            tensor cores as m16n8k8 TF32 MMAs with split
+                            operands (3xTF32, FP32-accurate products);
+                            0 = every unit on the FP32 pipes; -1 = the
+                            default (see mase_default_options)           */
 } mase_options;
 
 /* Per-solve results.  Arrays are host arrays of n_snap entries supplied by

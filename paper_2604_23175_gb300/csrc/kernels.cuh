@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace mase_dev {
 
 
@@ -77,6 +79,8 @@ struct Tables {
     const int4 *chunk_rec;  // 2 int4 per 32-row panel chunk
     const int *lev_chunks;
     int wait_polls;         // polls of a dataflow wait before it gives up (error bit 4)
+    int mma_min_w;          // FP32 factors: update units of panels at least this wide run
+                            // on the tensor cores (3xTF32 MMA); 0 = SIMT units only
 };
 
 struct StopRule {
@@ -538,6 +542,89 @@ __device__ __forceinline__ void unit_rows(const ST &st, RS *y, const RG *Ps, con
         unit_pass<RG, RS, NJ, 1, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, i0, lane);
 }
 
+// Update unit on the tensor cores (FP32 factors only): the same products as
+// unit_rows, as warp-level m16n8k8 TF32 MMAs.  A is the unit's rows of the
+// panel (16 rows per tile, the panel's columns as k), B holds the unit's
+// target columns (n = 0..nj-1) and, in n = 4, the supernode's rhs values, so
+// that the rhs update rides along.  Each operand is split into a TF32 high
+// part and a TF32 remainder, and hi*hi + hi*lo + lo*hi are accumulated in
+// FP32 ("3xTF32"), which keeps the products at FP32 accuracy (a single TF32
+// product would carry a 2^-11 relative error into the Gauss-Newton step).
+// Results are scattered like unit_rows's: the lane holding (row, n) adds it
+// to the target through the relative-index map (n < nj, lower triangle) or
+// to the rhs row (n = 4, rows below rhs_end).
+__device__ __forceinline__ unsigned tf32_hi(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+template <int KS, class ST>
+__device__ __forceinline__ void unit_mma(const ST &st, float *y, const float *Ps, const int *relp,
+                                         const int *rws, const float *yc, int w, int ld, int j0,
+                                         int nj, int rhs_end, const int (&cb)[4], int lane) {
+    const int R = ld - w;
+    const int g = lane >> 2, t = lane & 3;
+    // B fragments: b0 = B[k = t][n = g], b1 = B[k = t + 4][n = g] of each k-step
+    unsigned bh[KS][2], bl[KS][2];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 8 * ks + t + 4 * h;
+            float b = 0.f;
+            if (k < w) {
+                if (g < nj) b = Ps[(size_t)k * ld + j0 + g];
+                else if (g == 4 && rhs_end > 0) b = yc[k];
+            }
+            bh[ks][h] = tf32_hi(b);
+            bl[ks][h] = tf32_hi(b - __uint_as_float(bh[ks][h]));
+        }
+    for (int r0 = j0; r0 < R; r0 += 16) {
+        const int ra = r0 + g, rb = r0 + g + 8;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            // a0 = A[g][t], a1 = A[g + 8][t], a2 = A[g][t + 4], a3 = A[g + 8][t + 4]
+            const int k0 = 8 * ks + t, k1 = k0 + 4;
+            const float x0 = (ra < R && k0 < w) ? Ps[(size_t)k0 * ld + ra] : 0.f;
+            const float x1 = (rb < R && k0 < w) ? Ps[(size_t)k0 * ld + rb] : 0.f;
+            const float x2 = (ra < R && k1 < w) ? Ps[(size_t)k1 * ld + ra] : 0.f;
+            const float x3 = (rb < R && k1 < w) ? Ps[(size_t)k1 * ld + rb] : 0.f;
+            const unsigned ah[4] = {tf32_hi(x0), tf32_hi(x1), tf32_hi(x2), tf32_hi(x3)};
+            const unsigned al[4] = {tf32_hi(x0 - __uint_as_float(ah[0])), tf32_hi(x1 - __uint_as_float(ah[1])),
+                                    tf32_hi(x2 - __uint_as_float(ah[2])), tf32_hi(x3 - __uint_as_float(ah[3]))};
+            mma_tf32(acc, al, bh[ks][0], bh[ks][1]);
+            mma_tf32(acc, ah, bl[ks][0], bl[ks][1]);
+            mma_tf32(acc, ah, bh[ks][0], bh[ks][1]);
+        }
+        // c0 = C[g][2t], c1 = C[g][2t + 1], c2 = C[g + 8][2t], c3 = C[g + 8][2t + 1]
+        if (t < 2) {
+            const int n0 = 2 * t, n1 = n0 + 1;
+            if (ra < R) {
+                const int tr = relp[ra];
+                if (n0 < nj && ra >= j0 + n0) atomicAdd(st.at(cb[n0] + tr), -acc[0]);
+                if (n1 < nj && ra >= j0 + n1) atomicAdd(st.at(cb[n1] + tr), -acc[1]);
+            }
+            if (rb < R) {
+                const int tr = relp[rb];
+                if (n0 < nj && rb >= j0 + n0) atomicAdd(st.at(cb[n0] + tr), -acc[2]);
+                if (n1 < nj && rb >= j0 + n1) atomicAdd(st.at(cb[n1] + tr), -acc[3]);
+            }
+        } else if (t == 2) {
+            if (ra < rhs_end) atomicAdd(y + rws[ra], -acc[0]);
+            if (rb < rhs_end) atomicAdd(y + rws[rb], -acc[2]);
+        }
+    }
+}
+
 // Task bodies are kept out of line so that each gets the whole register file
 // for its own tile (a diagonal tile of up to 16 columns lives in 16 registers
 // per lane) and no tile spills.
@@ -563,7 +650,7 @@ __device__ __noinline__ void task_panel(const ST st, int off, int w, int ld, int
 }
 template <class RG, class RS, class ST>
 __device__ __noinline__ void task_unit(const ST st, RS *y, const int *rel, const int *rows,
-                                       const int4 q1, const int4 q2, const int4 q3) {
+                                       const int4 q1, const int4 q2, const int4 q3, int mma_min_w) {
     const int lane = threadIdx.x & 31;
     const RG *Ps = st.at(q1.x);
     const int *relp = rel + q1.y;
@@ -572,6 +659,14 @@ __device__ __noinline__ void task_unit(const ST st, RS *y, const int *rel, const
     const int w = q2.x & 0xff, nj = q2.x >> 8, ld = q2.y & 0xffff, j0 = q2.y >> 16;
     const int rhs_end = q2.z;
     const int cb[4] = {q2.w, q3.x, q3.y, q3.z};
+    if constexpr (std::is_same<RG, float>::value && std::is_same<RS, float>::value) {
+        if (mma_min_w > 0 && w >= mma_min_w) {
+            if (w <= 8) unit_mma<1, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, nj, rhs_end, cb, lane);
+            else if (w <= 16) unit_mma<2, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, nj, rhs_end, cb, lane);
+            else unit_mma<4, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, nj, rhs_end, cb, lane);
+            return;
+        }
+    }
     switch (nj) {
         case 1: unit_rows<RG, RS, 1, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
         case 2: unit_rows<RG, RS, 2, ST>(st, y, Ps, relp, rws, yc, w, ld, j0, rhs_end, cb, lane); break;
@@ -628,7 +723,7 @@ __device__ void factor_tasks(const FacDev &F, const Tables &T, const ST &st, RS 
         const int type = q0.x >> 24;
         if (type == 0) task_diag<RG, RS, ST>(st, q1.x, q1.y, q1.z, y + q1.w, err);
         else if (type == 1) task_panel<RG, ST>(st, q1.x, q1.y, q1.z, q1.w);
-        else task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3);
+        else task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3, T.mma_min_w);
         __syncwarp();
         if (lane == 0 && q0.w >= 0) {
             __threadfence_block();
@@ -662,7 +757,7 @@ __device__ void factor_levels(const FacDev &F, const Tables &T, const ST &st, RS
                 task_panel<RG, ST>(st, q1.x, q1.y, q1.z, q1.w);
             } else {
                 const int4 q2 = trec[4 * t + 2], q3 = trec[4 * t + 3];
-                task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3);
+                task_unit<RG, RS, ST>(st, y, rel, rows, q1, q2, q3, T.mma_min_w);
             }
         }
         tm.sync();

@@ -23,6 +23,8 @@ namespace {
 constexpr int kBackThreads = 256;
 // shared memory of one SM that blocks can use (228 KB, less 1 KB each)
 constexpr size_t kSmemPerSM = 228 * 1024;
+// narrowest source panel whose update units run on the tensor cores (MIXED)
+constexpr int kDefaultTensorUnits = 0;
 
 thread_local std::string g_last_error;
 
@@ -543,6 +545,7 @@ int build(mase_handle *h) {
     Tables &T = h->T;
     // a dependency wait gives up after this many unsatisfied polls (~0.2 s by default)
     T.wait_polls = h->opt.wait_polls > 0 ? h->opt.wait_polls : (1 << 22);
+    T.mma_min_w = h->opt.precision == MASE_MIXED ? h->opt.tensor_units : 0;
     T.sn_c0 = h->t_sn_c0.p; T.sn_w = h->t_sn_w.p; T.sn_nr = h->t_sn_nr.p; T.sn_off = h->t_sn_off.p;
     T.sn_order = h->t_sn_order.p;
     T.lev_off = h->t_lev_off.p; T.rows = h->t_rows.p;
@@ -983,6 +986,7 @@ void mase_default_options(mase_options *o) {
     o->wait_polls = 0;
     o->inner_iters = 0;
     o->autotune = 1;
+    o->tensor_units = kDefaultTensorUnits;
 }
 
 const char *mase_status_str(int code) {
@@ -1016,6 +1020,9 @@ int mase_create(const mase_network *net, const mase_partition *part, const mase_
     if (h->opt.inner_iters < 0 || h->opt.inner_iters > 8)
         return set_err(MASE_EINVAL, "bad inner iteration count");
     if (h->opt.wait_polls < 0) return set_err(MASE_EINVAL, "bad wait_polls");
+    if (h->opt.tensor_units == -1) h->opt.tensor_units = kDefaultTensorUnits;
+    if (h->opt.tensor_units < 0 || h->opt.tensor_units > 255)
+        return set_err(MASE_EINVAL, "tensor_units must be -1 or 0..255");
     int threads = h->opt.threads ? h->opt.threads : 512;
     if (threads < 64 || threads > 512 || threads % 32) return set_err(MASE_EINVAL, "bad threads");
     h->threads = threads;

@@ -45,7 +45,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("refine", C.c_int32), ("threads", C.c_int32), ("device", C.c_int32),
                 ("stream", C.c_void_p), ("profile", C.c_int32), ("wait_polls", C.c_int32),
-                ("inner_iters", C.c_int32), ("autotune", C.c_int32)]
+                ("inner_iters", C.c_int32), ("autotune", C.c_int32), ("tensor_units", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -262,7 +262,7 @@ class Estimator:
 
     def __init__(self, grid, sigma, n_snap: int, z=None, mask=None, precision=MIXED,
                  schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
-                 profile=False, wait_polls=0, inner_iters=0, autotune=True):
+                 profile=False, wait_polls=0, inner_iters=0, autotune=True, tensor_units=-1):
         self.lib = load()
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -274,6 +274,7 @@ class Estimator:
         opt.wait_polls = int(wait_polls)
         opt.inner_iters = int(inner_iters)
         opt.autotune = int(bool(autotune))
+        opt.tensor_units = int(tensor_units)
         meas = Measurements(int(n_snap), _ptr(z), sig.ctypes.data_as(_f64p), _ptr(mask))
         h = C.c_void_p()
         rc = self.lib.mase_create(C.byref(net), C.byref(part), C.byref(meas), C.byref(opt), C.byref(h))

@@ -109,6 +109,25 @@ def test_parity_fewer_warps_without_graphs(mase, threads):
     _check(net, g, x, res, z, w, range(2))
 
 
+@pytest.mark.parametrize("tensor_units", [1, 8, 16])
+@pytest.mark.parametrize("name", ["grid300_k4", "grid2869_k16"])
+def test_parity_tensor_core_units(mase, name, tensor_units):
+    """MIXED with the factorisation's update units on the tensor cores (3xTF32
+    MMA) for source panels at least tensor_units wide (1: every unit, in the
+    area factors and the coordinator): the oracle's estimates, and the FP32
+    units' iteration counts."""
+    g = synth.make_grid(name)
+    net, Vm, Va, z, sig = problem(g, 3, 3310)
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED,
+                  tensor_units=tensor_units)
+    assert res.rc == mase.MASE_OK, res
+    _check(net, g, x, res, z, w, range(3))
+    x0, res0 = _run(mase, g, sig, z, precision=mase.MIXED, schedule=mase.BATCHED, tensor_units=0)
+    assert np.array_equal(res.iters, res0.iters), (res.iters, res0.iters)
+    assert np.max(np.abs(x - x0)) <= 1e-8
+
+
 @pytest.mark.parametrize("refine", [0, 3])
 def test_parity_refinement_sweeps(mase, refine):
     """MIXED without the FP64 refinement of the boundary solve (an inexact

@@ -49,9 +49,9 @@ def _perturbed_start(g, Vm, Va, seed):
     return np.ascontiguousarray(x0)
 
 
-def _one_step(mase, g, sig, z, x0, precision, schedule):
+def _one_step(mase, g, sig, z, x0, precision, schedule, **kw):
     S = z.shape[0]
-    est = mase.Estimator(g, sig, S, z=z, precision=precision, schedule=schedule)
+    est = mase.Estimator(g, sig, S, z=z, precision=precision, schedule=schedule, **kw)
     x1 = np.zeros_like(x0)
     res = est.solve(x0=x0, tol=0.0, max_iter=1, x_out=x1, check=False)
     est.close()
@@ -96,12 +96,14 @@ def test_one_step_full_dx_fp64(mase, name, slack_b, schedule):
 
 
 @pytest.mark.parametrize("name,slack_b", [("grid2869_k16", True), ("grid9241_k32", False)])
-def test_one_step_full_dx_mixed(mase, name, slack_b):
+@pytest.mark.parametrize("tensor_units", [0, 1])
+def test_one_step_full_dx_mixed(mase, name, slack_b, tensor_units):
     g, sig, z, x0, dx_ref = _step_case(name, slack_b)
-    dx = _one_step(mase, g, sig, z, x0, mase.MIXED, mase.BATCHED)
+    dx = _one_step(mase, g, sig, z, x0, mase.MIXED, mase.BATCHED, tensor_units=tensor_units)
     for s in range(z.shape[0]):
         err = np.max(np.abs(dx[s] - dx_ref[s])) / np.max(np.abs(dx_ref[s]))
-        print(f"MIXED one-step relative error {name} slack_on_boundary={slack_b} snapshot {s}: {err:.3e}")
+        print(f"MIXED one-step relative error {name} slack_on_boundary={slack_b} "
+              f"tensor_units={tensor_units} snapshot {s}: {err:.3e}")
         assert err <= STEP_RTOL_MIXED, (s, err)
 
 
@@ -130,13 +132,16 @@ def _bench_case():
     return _BENCH["v"]
 
 
-@pytest.mark.parametrize("precision,schedule", [("MIXED", "BATCHED"), ("FP64", "PER_AREA")])
-def test_parity_9241_bus_all_64_snapshots(mase, precision, schedule):
+@pytest.mark.parametrize("precision,schedule,tensor_units", [("MIXED", "BATCHED", -1), ("FP64", "PER_AREA", -1),
+                                                            ("MIXED", "BATCHED", 0), ("MIXED", "BATCHED", 1)])
+def test_parity_9241_bus_all_64_snapshots(mase, precision, schedule, tensor_units):
     """Every snapshot of the benchmark workload (9241-bus shape, 32 areas,
-    64-step random walk) in the launch configuration the benchmark times."""
+    64-step random walk) in the launch configuration the benchmark times
+    (tensor_units -1: the library's default), and with the update units all
+    on the FP32 pipes (0) or all on the tensor cores (1)."""
     g, net, z, sig, w, refs = _bench_case()
     est = mase.Estimator(g, sig, 64, z=z, precision=getattr(mase, precision),
-                         schedule=getattr(mase, schedule))
+                         schedule=getattr(mase, schedule), tensor_units=tensor_units)
     x = np.zeros((64, 2 * g.n_bus))
     res = est.solve(tol=1e-8, max_iter=10, x_out=x, check=False)
     est.close()
