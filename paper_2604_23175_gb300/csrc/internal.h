@@ -62,6 +62,9 @@ void destroy_warmstart(WarmStart *w);
 int learned_start(mase_handle *h, int *launches);
 // per snapshot, 1 where the last learned start kept the networks' proposal
 const int *learned_picked(const mase_handle *h);
+// device flag set when a tensor-core GEMM of the learned start gave up a
+// bounded wait (nullptr before the first learned start)
+int *learned_gemm_err(const mase_handle *h);
 // Adds r^T W r at the states (xV, xT) to J[s] for every snapshot (area kernel
 // in objective mode); J must be zeroed by the caller.
 void launch_objective(mase_handle *h, double *xV, double *xT, double *J, int *launches);

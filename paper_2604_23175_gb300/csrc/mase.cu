@@ -862,6 +862,7 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     std::vector<int> iters(nS), status(nS), picked(nS, 0);
     std::vector<double> J(nS), last(nS);
     double acc[4] = {0, 0, 0, 0};
+    int gemm_err = 0;
     int steps = 0;
     // objective at the final states, the states out and the per-snapshot results
     auto finish = [&]() -> int {
@@ -885,9 +886,12 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
         CK(cudaMemcpyAsync(last.data(), h->laststep.p, nS * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(acc, h->clk_acc.p, sizeof(acc), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(&steps_now, h->steps_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        if (learned)
+        if (learned) {
             CK(cudaMemcpyAsync(picked.data(), mase_internal::learned_picked(h), nS * sizeof(int),
                                cudaMemcpyDeviceToHost, st));
+            if (int *ge = mase_internal::learned_gemm_err(h))
+                CK(cudaMemcpyAsync(&gemm_err, ge, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
         CK(cudaEventRecord(ev[5], st));
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
@@ -900,6 +904,10 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     if (rc != MASE_OK) return rc;
     rc = finish();
     if (rc != MASE_OK) return rc;
+    if (gemm_err) {
+        CK(cudaMemsetAsync(mase_internal::learned_gemm_err(h), 0, sizeof(int), st));
+        return set_err(MASE_EDEVICE, "a tensor-core GEMM of the learned start gave up a bounded wait");
+    }
     // flat-start fallback: a snapshot that started from the networks'
     // proposal and whose factor broke down (non-positive pivot or non-finite
     // step) is solved again from the flat start; its iteration count keeps
