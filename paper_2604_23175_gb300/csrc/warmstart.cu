@@ -64,8 +64,6 @@ struct GemmProb {
 
 enum { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DGELU = 2, EPI_GRAD = 3 };
 
-constexpr int TB = 64, TK = 32, TPAD = 40;
-
 __device__ __forceinline__ float gelu_f(float u) {
     return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f));
 }
@@ -74,121 +72,17 @@ __device__ __forceinline__ float gelu_grad_f(float u) {
            u * 0.39894228040143268f * expf(-0.5f * u * u);
 }
 
-// 64 x 32 tile of an operand into shared memory as S[row][k] (k contiguous).
-// All dimensions and offsets are multiples of 8 elements, so every 16-byte
-// chunk is either wholly inside or wholly outside the operand.
-__device__ __forceinline__ void load_tile(bf16 (*S)[TPAD], const bf16 *G, long long ld, int kmajor,
-                                          int r0, int k0, int R, int Kd, int tid) {
-    if (kmajor) {
-        for (int c = tid; c < 256; c += 128) {
-            const int r = c >> 2, kc = (c & 3) * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (r0 + r < R && k0 + kc < Kd) v = *(const uint4 *)(G + (long long)(r0 + r) * ld + k0 + kc);
-            *(uint4 *)&S[r][kc] = v;
-        }
-    } else {
-        for (int c = tid; c < 256; c += 128) {
-            const int k = c >> 3, rc = (c & 7) * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (k0 + k < Kd && r0 + rc < R) v = *(const uint4 *)(G + (long long)(k0 + k) * ld + r0 + rc);
-            const bf16 *e = (const bf16 *)&v;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) S[rc + i][k] = e[i];
-        }
-    }
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *p) {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm_bf16(const GemmProb *__restrict__ probs) {
-    const GemmProb p = probs[blockIdx.z];
-    const int m0 = blockIdx.y * TB, n0 = blockIdx.x * TB;
-    if (m0 >= p.M || n0 >= p.N) return;
-    __shared__ __align__(16) bf16 As[TB][TPAD];
-    __shared__ __align__(16) bf16 Bs[TB][TPAD];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    for (int k0 = 0; k0 < p.K; k0 += TK) {
-        load_tile(As, p.A, p.lda, p.a_km, m0, k0, p.M, p.K, tid);
-        load_tile(Bs, p.B, p.ldb, p.b_km, n0, k0, p.N, p.K, tid);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < TK; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-                ldmatrix_x4(a[mi], &As[wm + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int ni = 0; ni < 4; ni += 2) {
-                uint32_t r[4];
-                ldmatrix_x4(r, &Bs[wn + ni * 8 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
-                b[ni][0] = r[0];
-                b[ni][1] = r[1];
-                b[ni + 1][0] = r[2];
-                b[ni + 1][1] = r[3];
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = m0 + wm + mi * 16 + (lane >> 2) + (q >> 1) * 8;
-                const int c = n0 + wn + ni * 8 + (lane & 3) * 2 + (q & 1);
-                if (r >= p.M || c >= p.N) continue;
-                const float v = acc[mi][ni][q];
-                if (EPI == EPI_HIDDEN) {
-                    const float pre = v + p.bias[c];
-                    p.P_out[(long long)r * p.ldp + c] = __float2bfloat16(pre);
-                    p.Cb[(long long)r * p.ldc + c] = __float2bfloat16(gelu_f(pre));
-                } else if (EPI == EPI_OUT) {
-                    p.Cf[(long long)r * p.ldc + c] = v + p.bias[c];
-                } else if (EPI == EPI_DGELU) {
-                    const float pre = __bfloat162float(p.P_in[(long long)r * p.ldp + c]);
-                    p.Cb[(long long)r * p.ldc + c] = __float2bfloat16(v * gelu_grad_f(pre));
-                } else {
-                    p.Cf[(long long)r * p.ldc + c] = v;
-                }
-            }
-}
-
 // ---------------------------------------------------------------------------
 // forward layers on the 5th-generation tensor cores (tcgen05)
 // ---------------------------------------------------------------------------
-// C(M x N) = A(M x K) * B(N x K)^T, both operands K-major (activations and
-// weights as stored), one problem per blockIdx.z.  A block of 128 threads
+// C(M x N) = A(M x K) * B(K x N), one problem per blockIdx.z, with the
+// epilogues of the MLP: bias (+ GELU) for the forward layers, the GELU
+// derivative for the backward data products, plain FP32 for the weight
+// gradients.  Operands may be stored K-contiguous or M/N-contiguous (GemmProb).  A block of 128 threads
 // owns a 128 x 128 output tile: its accumulator lives in 128 TMEM columns
 // (row i of the tile in TMEM lane i, FP32), operand tiles of 64 K-columns
-// are staged by cp.async into a 3-deep ring of shared-memory buffers in the
-// canonical K-major layout without swizzle (8-row x 16-byte core matrices),
+// are staged into a 3-deep ring of shared-memory buffers in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices),
 // one thread issues the four K = 16 MMAs of a stage and commits them to the
 // stage's mbarrier, which frees the buffer for the next tile.  The epilogue
 // reads the accumulator back with tcgen05.ld (warp w: rows 32w..32w+31) and
@@ -305,21 +199,35 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(gsm + STAGES * STAGE_BYTES + 8 * STAGES);
     const int ra = min(MT, p.M - m0), rb = min(NT, p.N - n0);
     const int nk = (p.K + KT - 1) / KT;
+    // one operand's 64 K-columns of rows [r0, r0 + nr) into the staging tile
+    // at ts: K-contiguous rows go by cp.async 16 bytes at a time; rows
+    // contiguous along M/N (km = 0) are read 8 rows at a time and transposed
+    // into the tile by 2-byte stores; K-columns beyond K are zeros
+    auto load_op = [&](uint32_t ts, unsigned char *tp, const bf16 *X, long long ld, int km, int r0, int nr,
+                       int k0) {
+        if (km) {
+            for (int c = tid; c < nr * 8; c += 128) {
+                const int r = c >> 3, kc = c & 7, k = k0 + kc * 8;
+                const bool in = k < p.K;
+                cp_async16(ts + tile_off(r, kc), in ? (const void *)(X + (long long)(r0 + r) * ld + k) : (const void *)X,
+                           in ? 16 : 0);
+            }
+        } else {
+            for (int c = tid; c < (nr >> 3) * KT; c += 128) {
+                const int kl = c % KT, rg = (c / KT) * 8, k = k0 + kl;
+                uint4 u = make_uint4(0u, 0u, 0u, 0u);
+                if (k < p.K) u = *reinterpret_cast<const uint4 *>(X + (long long)k * ld + r0 + rg);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<bf16 *>(tp + tile_off(rg + i, kl >> 3) + (kl & 7) * 2) = e[i];
+            }
+        }
+    };
     auto load = [&](int kt) {
-        const uint32_t a_s = sbase + (uint32_t)(kt % STAGES) * STAGE_BYTES, b_s = a_s + A_BYTES;
-        const int k0 = kt * KT;
-        for (int c = tid; c < ra * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7, k = k0 + kc * 8;
-            const bool in = k < p.K;
-            cp_async16(a_s + tile_off(r, kc), in ? (const void *)(p.A + (long long)(m0 + r) * p.lda + k) : (const void *)p.A,
-                       in ? 16 : 0);
-        }
-        for (int c = tid; c < rb * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7, k = k0 + kc * 8;
-            const bool in = k < p.K;
-            cp_async16(b_s + tile_off(r, kc), in ? (const void *)(p.B + (long long)(n0 + r) * p.ldb + k) : (const void *)p.B,
-                       in ? 16 : 0);
-        }
+        const uint32_t off = (uint32_t)(kt % STAGES) * STAGE_BYTES;
+        load_op(sbase + off, gsm + off, p.A, p.lda, p.a_km, m0, ra, kt * KT);
+        load_op(sbase + off + A_BYTES, gsm + off + A_BYTES, p.B, p.ldb, p.b_km, n0, rb, kt * KT);
     };
     bool ok = true;
     // two tiles in flight ahead of the MMAs (one commit group per tile, empty
@@ -385,9 +293,25 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
                     *reinterpret_cast<uint4 *>(po + j) = *reinterpret_cast<const uint4 *>(pa);
                     *reinterpret_cast<uint4 *>(co + j) = *reinterpret_cast<const uint4 *>(ca);
                 }
+            } else if (EPI == EPI_DGELU) {
+                const bf16 *pi = p.P_in + (long long)row * p.ldp + cb;
+                bf16 *co = p.Cb + (long long)row * p.ldc + cb;
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    if (j >= nc) break;
+                    const uint4 pu = *reinterpret_cast<const uint4 *>(pi + j);
+                    const bf16 *pe = reinterpret_cast<const bf16 *>(&pu);
+                    __align__(16) bf16 ca[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ca[q] = __float2bfloat16(v[j + q] * gelu_grad_f(__bfloat162float(pe[q])));
+                    *reinterpret_cast<uint4 *>(co + j) = *reinterpret_cast<const uint4 *>(ca);
+                }
             } else {
                 float *co = p.Cf + (long long)row * p.ldc + cb;
-                for (int j = 0; j < nc; ++j) co[j] = v[j] + p.bias[cb + j];
+                if (EPI == EPI_OUT)
+                    for (int j = 0; j < nc; ++j) co[j] = v[j] + p.bias[cb + j];
+                else
+                    for (int j = 0; j < nc; ++j) co[j] = v[j];
             }
         }
     } else if (tid == 0) {
@@ -824,6 +748,8 @@ int build_workspace(mase_handle *h, WarmStart &W, Workspace &ws, int B, bool tra
         WK(cudaMemsetAsync(W.gemm_err.p, 0, sizeof(int), st));
         WK(cudaFuncSetAttribute(k_gemm_tc<EPI_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
         WK(cudaFuncSetAttribute(k_gemm_tc<EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
+        WK(cudaFuncSetAttribute(k_gemm_tc<EPI_DGELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
+        WK(cudaFuncSetAttribute(k_gemm_tc<EPI_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM));
     }
     const int K = W.K, Hd = W.Hd;
     const long long HB = (long long)K * Hd;
@@ -1002,13 +928,13 @@ void backward(mase_handle *h, WarmStart &W, Workspace &ws) {
     for (int l = 3; l >= 0; --l) {
         const int mmax = l == 3 ? max_dim(W, 3, true) : W.Hd;
         const int nmax = max_dim(W, l, false);
-        dim3 gw((nmax + TB - 1) / TB, (mmax + TB - 1) / TB, W.K);
-        k_gemm_bf16<EPI_GRAD><<<gw, 128, 0, st>>>(ws.bwdw[l].p);
+        dim3 gw((nmax + tcg::NT - 1) / tcg::NT, (mmax + tcg::MT - 1) / tcg::MT, W.K);
+        k_gemm_tc<EPI_GRAD><<<gw, 128, tcg::SMEM, st>>>(ws.bwdw[l].p, W.gemm_err.p);
         if (l == 3) k_colsum<float><<<grid_for(W.OS), 256, 0, st>>>(ws.dYf.p, B, W.OS, ws.colmap[3].p, W.grad.p);
         else k_colsum<bf16><<<grid_for(HB), 256, 0, st>>>(ws.dA.p + (long long)l * B * HB, B, HB, ws.colmap[l].p, W.grad.p);
         if (l > 0) {
-            dim3 gd((W.Hd + TB - 1) / TB, (B + TB - 1) / TB, W.K);
-            k_gemm_bf16<EPI_DGELU><<<gd, 128, 0, st>>>(ws.bwdd[l - 1].p);
+            dim3 gd((W.Hd + tcg::NT - 1) / tcg::NT, (B + tcg::MT - 1) / tcg::MT, W.K);
+            k_gemm_tc<EPI_DGELU><<<gd, 128, tcg::SMEM, st>>>(ws.bwdd[l - 1].p, W.gemm_err.p);
         }
     }
 }
