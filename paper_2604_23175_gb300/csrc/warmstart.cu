@@ -82,7 +82,8 @@ __device__ __forceinline__ float gelu_grad_f(float u) {
 // owns a 128 x 128 output tile: its accumulator lives in 128 TMEM columns
 // (row i of the tile in TMEM lane i, FP32), operand tiles of 64 K-columns
 // are staged into a 3-deep ring of shared-memory buffers in the canonical
-// K-major layout without swizzle (8-row x 16-byte core matrices),
+// K-major layout without swizzle (8-row x 16-byte core matrices; operands
+// stored contiguous along M or N are transposed on the way in),
 // one thread issues the four K = 16 MMAs of a stage and commits them to the
 // stage's mbarrier, which frees the buffer for the next tile.  The epilogue
 // reads the accumulator back with tcgen05.ld (warp w: rows 32w..32w+31) and
@@ -213,14 +214,46 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
                            in ? 16 : 0);
             }
         } else {
-            for (int c = tid; c < (nr >> 3) * KT; c += 128) {
-                const int kl = c % KT, rg = (c / KT) * 8, k = k0 + kl;
-                uint4 u = make_uint4(0u, 0u, 0u, 0u);
-                if (k < p.K) u = *reinterpret_cast<const uint4 *>(X + (long long)k * ld + r0 + rg);
-                const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+            // a thread takes an 8 (k) x 8 (row) block: eight 16-byte loads
+            // along the rows (consecutive threads, consecutive row groups),
+            // an in-register transpose of 16-bit pairs, and eight 16-byte
+            // stores, one core-matrix row each, in an order rotated by the
+            // thread so that a warp's stores spread over the banks
+            const int nrg = nr >> 3;
+            for (int c = tid; c < nrg * (KT / 8); c += 128) {
+                const int rb = (c % nrg) * 8, kb = (c / nrg) * 8;
+                uint32_t u[8][4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<bf16 *>(tp + tile_off(rg + i, kl >> 3) + (kl & 7) * 2) = e[i];
+                for (int j = 0; j < 8; ++j) {
+                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                    if (k0 + kb + j < p.K) q = *reinterpret_cast<const uint4 *>(X + (long long)(k0 + kb + j) * ld + r0 + rb);
+                    u[j][0] = q.x; u[j][1] = q.y; u[j][2] = q.z; u[j][3] = q.w;
+                }
+                // v[i] word p = (X(k = 2p, row i), X(k = 2p + 1, row i))
+                uint32_t v[8][4];
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v[2 * q][pp] = __byte_perm(u[2 * pp][q], u[2 * pp + 1][q], 0x5410);
+                        v[2 * q + 1][pp] = __byte_perm(u[2 * pp][q], u[2 * pp + 1][q], 0x7632);
+                    }
+#pragma unroll
+                for (int i0 = 0; i0 < 8; ++i0) {
+                    const int i = (i0 + c) & 7;
+                    uint4 w;
+                    switch (i) {   // registers are not dynamically indexable
+                        case 0: w = make_uint4(v[0][0], v[0][1], v[0][2], v[0][3]); break;
+                        case 1: w = make_uint4(v[1][0], v[1][1], v[1][2], v[1][3]); break;
+                        case 2: w = make_uint4(v[2][0], v[2][1], v[2][2], v[2][3]); break;
+                        case 3: w = make_uint4(v[3][0], v[3][1], v[3][2], v[3][3]); break;
+                        case 4: w = make_uint4(v[4][0], v[4][1], v[4][2], v[4][3]); break;
+                        case 5: w = make_uint4(v[5][0], v[5][1], v[5][2], v[5][3]); break;
+                        case 6: w = make_uint4(v[6][0], v[6][1], v[6][2], v[6][3]); break;
+                        default: w = make_uint4(v[7][0], v[7][1], v[7][2], v[7][3]); break;
+                    }
+                    *reinterpret_cast<uint4 *>(tp + tile_off(rb + i, kb >> 3)) = w;
+                }
             }
         }
     };
