@@ -1015,64 +1015,121 @@ __global__ void __launch_bounds__(512) k_local(const AreaDev *__restrict__ areas
         atomicAdd(st + T.own_gvv[A.own_base + o], RG(wv));
     }
     __syncthreads();
-    // ---- E3: flow rows; gradient of flow and injection rows; flow-row gain terms
-    for (int e = tid; e < n_ends; e += nt) {
-        const int ee = A.end_base + e;
-        const int qi = T.end_qi[ee], qj = T.end_qj[ee];
-        const double2 pq = *(const double2 *)(endbuf + (size_t)e * endstride);
-        const double wPe = wt(rPe + e), wQe = wt(rQe + e);
-        const double rPf = z[rPe + e] - pq.x, rQf = z[rQe + e] - pq.y;
-        Jloc += wPe * rPf * rPf + wQe * rQf * rQf;
-        const double Vi = bV[qi], Vj = bV[qj];
-        const double g_ = T.end_g[ee], b_ = T.end_b[ee], bh_ = T.end_bh[ee];
-        const double2 tr = end_trig(bC[qi], bS[qi], bC[qj], bS[qj], g_, b_);
-        const double gc_bs = tr.x, gs_bc = tr.y;
-        const double ViVj = Vi * Vj;
-        // partials w.r.t. (Vi, thi, Vj, thj)
-        double dP[4], dQ[4];
-        dP[0] = 2.0 * Vi * g_ - Vj * gc_bs;
-        dP[1] = ViVj * gs_bc;
-        dP[2] = -Vi * gc_bs;
-        dP[3] = -dP[1];
-        dQ[0] = -2.0 * Vi * (b_ + bh_) - Vj * gs_bc;
-        dQ[1] = -ViVj * gc_bs;
-        dQ[2] = -Vi * gs_bc;
-        dQ[3] = -dQ[1];
-        const int o = T.end_own[ee];
-        const double2 ij = inj[o];
-        const double aP = wPe * rPf + ij.x, aQ = wQe * rQf + ij.y;
-        const int *vv = T.end_var + 4 * (long long)ee;
+    // ---- E3: flow rows; gradient of flow and injection rows; flow-row gain terms.
+    // Ends are grouped by owning bus, so the lanes of a warp hold runs of ends
+    // of one bus: the terms every end of a bus adds to the same place (the
+    // bus's own gradient entries and diagonal gain block, its injection self
+    // partials) are summed over each run by a warp-level segmented reduction
+    // and added once per run; the terms aimed at the far bus are added per end.
+    {
+        constexpr unsigned FULL = 0xffffffffu;
+        const int lane = tid & 31;
+        for (int e0 = tid - lane; e0 < n_ends; e0 += nt) {
+            const int e = e0 + lane;
+            const bool valid = e < n_ends;
+            const int ee = A.end_base + (valid ? e : 0);
+            double own_g[2] = {0.0, 0.0};   // gradient of the own bus's V and theta
+            RG own_s[7];                     // gain (Vi,Vi), (Vi,thi), (thi,thi); self partials
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int v = vv[a];
-            if (v >= 0) atomicAdd(g + v, aP * dP[a] + aQ * dQ[a]);
-        }
-        RG hP[4], hQ[4];
+            for (int q = 0; q < 7; ++q) own_s[q] = RG(0);
+            int o = -1 - lane, gv0 = -1, gv1 = -1, gp0 = -1, gp1 = -1, gp4 = -1;
+            if (valid) {
+                const int qi = T.end_qi[ee], qj = T.end_qj[ee];
+                const double2 pq = *(const double2 *)(endbuf + (size_t)e * endstride);
+                const double wPe = wt(rPe + e), wQe = wt(rQe + e);
+                const double rPf = z[rPe + e] - pq.x, rQf = z[rQe + e] - pq.y;
+                Jloc += wPe * rPf * rPf + wQe * rQf * rQf;
+                const double Vi = bV[qi], Vj = bV[qj];
+                const double g_ = T.end_g[ee], b_ = T.end_b[ee], bh_ = T.end_bh[ee];
+                const double2 tr = end_trig(bC[qi], bS[qi], bC[qj], bS[qj], g_, b_);
+                const double gc_bs = tr.x, gs_bc = tr.y;
+                const double ViVj = Vi * Vj;
+                // partials w.r.t. (Vi, thi, Vj, thj)
+                double dP[4], dQ[4];
+                dP[0] = 2.0 * Vi * g_ - Vj * gc_bs;
+                dP[1] = ViVj * gs_bc;
+                dP[2] = -Vi * gc_bs;
+                dP[3] = -dP[1];
+                dQ[0] = -2.0 * Vi * (b_ + bh_) - Vj * gs_bc;
+                dQ[1] = -ViVj * gc_bs;
+                dQ[2] = -Vi * gs_bc;
+                dQ[3] = -dQ[1];
+                o = T.end_own[ee];
+                const double2 ij = inj[o];
+                const double aP = wPe * rPf + ij.x, aQ = wQe * rQf + ij.y;
+                const int *vv = T.end_var + 4 * (long long)ee;
+                gv0 = vv[0];
+                gv1 = vv[1];
+                own_g[0] = aP * dP[0] + aQ * dQ[0];
+                own_g[1] = aP * dP[1] + aQ * dQ[1];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            hP[a] = RG(dP[a]);
-            hQ[a] = RG(dQ[a]);
-        }
-        const RG wp = RG(wPe), wq = RG(wQe);
-        const int *gp = T.end_gpos + 10 * (long long)ee;
-        int idx = 0;
+                for (int a = 2; a < 4; ++a) {
+                    const int v = vv[a];
+                    if (v >= 0) atomicAdd(g + v, aP * dP[a] + aQ * dQ[a]);
+                }
+                RG hP[4], hQ[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a) {
+                    hP[a] = RG(dP[a]);
+                    hQ[a] = RG(dQ[a]);
+                }
+                const RG wp = RG(wPe), wq = RG(wQe);
+                const int *gp = T.end_gpos + 10 * (long long)ee;
+                int idx = 0;
 #pragma unroll
-            for (int c = a; c < 4; ++c, ++idx) {
-                const int p = gp[idx];
-                if (p >= 0) atomicAdd(st + p, wp * hP[a] * hP[c] + wq * hQ[a] * hQ[c]);
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = a; c < 4; ++c, ++idx) {
+                        const RG v = wp * hP[a] * hP[c] + wq * hQ[a] * hQ[c];
+                        if (idx == 0) { own_s[0] = v; gp0 = gp[0]; }
+                        else if (idx == 1) { own_s[1] = v; gp1 = gp[1]; }
+                        else if (idx == 4) { own_s[2] = v; gp4 = gp[4]; }
+                        else {
+                            const int p = gp[idx];
+                            if (p >= 0) atomicAdd(st + p, v);
+                        }
+                    }
+                // injection partials: own-bus part summed per bus, neighbour part kept per end
+                own_s[3] = hP[0];
+                own_s[4] = hP[1];
+                own_s[5] = hQ[0];
+                own_s[6] = hQ[1];
+                RG *nb = (RG *)(endbuf + (size_t)e * endstride);
+                nb[0] = hP[2];
+                nb[1] = hP[3];
+                nb[2] = hQ[2];
+                nb[3] = hQ[3];
             }
-        // injection partials: own-bus part summed per bus, neighbour part kept per end
-        atomicAdd(self + 4 * o + 0, hP[0]);
-        atomicAdd(self + 4 * o + 1, hP[1]);
-        atomicAdd(self + 4 * o + 2, hQ[0]);
-        atomicAdd(self + 4 * o + 3, hQ[1]);
-        RG *nb = (RG *)(endbuf + (size_t)e * endstride);
-        nb[0] = hP[2];
-        nb[1] = hP[3];
-        nb[2] = hQ[2];
-        nb[3] = hQ[3];
+            // runs of one owning bus: heads and each lane's run end
+            const int kprev = __shfl_up_sync(FULL, o, 1);
+            const bool head = lane == 0 || kprev != o;
+            const unsigned heads = __ballot_sync(FULL, head);
+            const unsigned later = lane == 31 ? 0u : (heads & (0xFFFFFFFEu << lane));
+            const int run_end = later ? __ffs(later) - 2 : 31;
+            const int longest = (int)__reduce_max_sync(FULL, (unsigned)(run_end - lane + 1));
+            for (int d = 1; d < longest; d <<= 1) {
+                const bool take = lane + d <= run_end;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const double t = __shfl_down_sync(FULL, own_g[q], d);
+                    if (take) own_g[q] += t;
+                }
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    const RG t = __shfl_down_sync(FULL, own_s[q], d);
+                    if (take) own_s[q] += t;
+                }
+            }
+            if (valid && head) {
+                if (gv0 >= 0) atomicAdd(g + gv0, own_g[0]);
+                if (gv1 >= 0) atomicAdd(g + gv1, own_g[1]);
+                if (gp0 >= 0) atomicAdd(st + gp0, own_s[0]);
+                if (gp1 >= 0) atomicAdd(st + gp1, own_s[1]);
+                if (gp4 >= 0) atomicAdd(st + gp4, own_s[2]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) atomicAdd(self + 4 * o + q, own_s[3 + q]);
+            }
+        }
     }
     __syncthreads();
     // ---- E4: injection-row gain terms, one item per pair of buses in the row

@@ -237,6 +237,7 @@ def test_repeat_solves_and_launch_counts(mase):
     g = synth.make_grid("grid2869_k16")
     net, Vm, Va, z, sig = problem(g, 2, 4000)
     est = mase.Estimator(g, sig, 2, z=z, precision=mase.MIXED, schedule=mase.BATCHED)
+    classes = est.info()["local_classes"]
     x1 = np.zeros((2, 2 * g.n_bus))
     x2 = np.zeros_like(x1)
     r1 = est.solve(tol=1e-8, max_iter=20, x_out=x1)
@@ -247,8 +248,9 @@ def test_repeat_solves_and_launch_counts(mase):
     # agree to within the stopping tolerance
     assert np.max(np.abs(x1 - x2)) < 1e-8
     it = int(r1.iters.max())
-    # reset + state-in + 4 per step (local, boundary, back, bookkeeping) + objective + state-out
-    assert r1.launches == 2 + 4 * it + 2
+    # reset + state-in + per step (one area-kernel launch per autotuned class,
+    # boundary, back, bookkeeping) + objective + state-out
+    assert r1.launches == 2 + (classes + 3) * it + 2
 
 
 def test_stage_times_account_for_the_solve(mase):
