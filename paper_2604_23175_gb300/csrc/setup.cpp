@@ -888,6 +888,53 @@ bool build_setup(const NetIn &net, int K, const int32_t *area_of_bus, Setup &st,
             for (int p : A.end_gpos)
                 if (p >= 0) ++gup;
             A.n_items = (int)A.item_own.size();
+            // A warp adds the gain terms of 32 consecutive items with one atomic
+            // instruction per slot, and lanes on one address serialise.  Items of
+            // different rows that share a gain entry (a bus pair in the
+            // injection rows of both buses) are spread over different windows
+            // of 32: each window takes, in order, the earliest remaining items
+            // whose entries are new to it.
+            {
+                const int n = A.n_items;
+                std::vector<int> order;
+                order.reserve(n);
+                std::vector<char> placed(n, 0);
+                std::vector<int> seen;   // entries of the current window
+                int first = 0;
+                while ((int)order.size() < n) {
+                    seen.clear();
+                    int cnt = 0;
+                    for (int i = first; i < n && cnt < 32; ++i) {
+                        if (placed[i]) continue;
+                        const int *p4 = &A.item_pos[4 * (size_t)i];
+                        bool clash = false;
+                        for (int a = 0; a < 4 && !clash; ++a)
+                            if (p4[a] >= 0 && std::find(seen.begin(), seen.end(), p4[a]) != seen.end())
+                                clash = true;
+                        if (clash) continue;
+                        for (int a = 0; a < 4; ++a)
+                            if (p4[a] >= 0) seen.push_back(p4[a]);
+                        placed[i] = 1;
+                        order.push_back(i);
+                        ++cnt;
+                    }
+                    while (first < n && placed[first]) ++first;
+                }
+                std::vector<int> rec(A.item_rec.size()), own(n), uv(n), pos(A.item_pos.size());
+                for (int j = 0; j < n; ++j) {
+                    const int i = order[j];
+                    for (int a = 0; a < 4; ++a) {
+                        rec[4 * (size_t)j + a] = A.item_rec[4 * (size_t)i + a];
+                        pos[4 * (size_t)j + a] = A.item_pos[4 * (size_t)i + a];
+                    }
+                    own[j] = A.item_own[i];
+                    uv[j] = A.item_uv[i];
+                }
+                A.item_rec.swap(rec);
+                A.item_own.swap(own);
+                A.item_uv.swap(uv);
+                A.item_pos.swap(pos);
+            }
             A.g_updates = gup;
             // boundary selector E_k (Eq. Ek_select)
             A.ebnd.assign(A.n_bnd, -1);
