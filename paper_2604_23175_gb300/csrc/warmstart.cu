@@ -182,8 +182,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(gsm);
     const uint32_t bar0 = sbase + STAGES * STAGE_BYTES;      // STAGES mbarriers (8 B each)
     const uint32_t tslot = bar0 + 8 * STAGES;                 // TMEM address written by tcgen05.alloc
-    for (int i = tid; i < STAGES * STAGE_BYTES / 16; i += 128)
-        reinterpret_cast<uint4 *>(gsm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // rows past M (A) or N (B) are never loaded: zero them once in every stage
+    {
+        const int ra0 = min(MT, p.M - m0), rb0 = min(NT, p.N - n0);
+        const int za = (MT - ra0) * 8, zb = (NT - rb0) * 8;   // 16-byte chunks per stage
+        for (int c = tid; c < STAGES * (za + zb); c += 128) {
+            const int stg = c / (za + zb), q = c % (za + zb);
+            const int r = q < za ? ra0 + (q >> 3) : rb0 + ((q - za) >> 3), kc = q & 7;
+            unsigned char *base = gsm + stg * STAGE_BYTES + (q < za ? 0 : A_BYTES);
+            *reinterpret_cast<uint4 *>(base + tile_off(r, kc)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -340,11 +349,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
                     *reinterpret_cast<uint4 *>(co + j) = *reinterpret_cast<const uint4 *>(ca);
                 }
             } else {
+                // FP32 out: N and ldc are multiples of 8, so are the chunks
                 float *co = p.Cf + (long long)row * p.ldc + cb;
-                if (EPI == EPI_OUT)
-                    for (int j = 0; j < nc; ++j) co[j] = v[j] + p.bias[cb + j];
-                else
-                    for (int j = 0; j < nc; ++j) co[j] = v[j];
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    if (j >= nc) break;
+                    float4 q = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (EPI == EPI_OUT) {
+                        q.x += p.bias[cb + j];
+                        q.y += p.bias[cb + j + 1];
+                        q.z += p.bias[cb + j + 2];
+                        q.w += p.bias[cb + j + 3];
+                    }
+                    *reinterpret_cast<float4 *>(co + j) = q;
+                }
             }
         }
     } else if (tid == 0) {
