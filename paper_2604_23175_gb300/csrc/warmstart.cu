@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmProb *__restrict__
     const GemmProb p = probs[blockIdx.z];
     const int m0 = blockIdx.y * MT, n0 = blockIdx.x * NT;
     if (m0 >= p.M || n0 >= p.N) return;
+    if (p.K <= 0) {   // no problem of the library has an empty K; refuse rather than read an empty accumulator
+        if (threadIdx.x == 0) atomicOr(err, 1);
+        return;
+    }
     extern __shared__ __align__(128) unsigned char gsm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(gsm);
