@@ -160,7 +160,7 @@ typedef struct {
                              from device clocks (first block start to last block end
                              of the stage's launches), or from CUDA events around the
                              stage's kernels with options.profile; [4] learned start (inference
-                             and its judge); [5] the rest outside the loop (reset,
+                             and its objective test); [5] the rest outside the loop (reset,
                              state in/out, objective pass, result copies); [6] time
                              inside the loop outside the stages' kernels (launch gaps,
                              and the per-step host round trip when use_graph = 0).

@@ -162,7 +162,7 @@ struct mase_handle {
     StopRule *h_stop = nullptr;   // pinned
     mase_info info{};
     mase_internal::WarmStart *ws = nullptr;   // learned warm start, if trained or loaded
-    DevBuf<double> xV2, xT2;                  // learned start kept while the flat start is judged
+    DevBuf<double> xV2, xT2;                  // learned start kept while the flat start's J is formed
 
     ~mase_handle() {
         mase_internal::destroy_warmstart(ws);

@@ -1023,7 +1023,7 @@ int ingest_chunk(mase_handle *h, const double *z_can, const uint8_t *mask_can, c
 const int *learned_picked(const mase_handle *h) { return h->ws ? h->ws->picked.p : nullptr; }
 int *learned_gemm_err(const mase_handle *h) { return h->ws ? h->ws->gemm_err.p : nullptr; }
 
-// learned start for the handle's current batch, judged against the flat start
+// learned start for the handle's current batch, kept per snapshot where its J is below the flat start's
 int learned_start(mase_handle *h, int *launches) {
     WarmStart *W = h->ws;
     if (!W || !W->ready) return fail(MASE_ENOTREADY, "no trained warm-start model");
