@@ -192,6 +192,20 @@ def workload_inputs(args):
     return g, Vm, Va, e, sig
 
 
+def workload_desc(args, g, S):
+    """Name of the workload a run times: the benchmark's own, or the variant
+    the flags select."""
+    variant = bool(args.workload != WORKLOAD or S != N_SNAP or args.areas or args.family or args.drop
+                   or args.inner_iters or args.tensor_units >= 0)
+    if not variant:
+        return WORKLOAD_DESC
+    return (f"{g.name} x{S} snapshots" + (f", {args.family} rows dropped" if args.family else "")
+            + (f", {100 * args.drop:g}% rows dropped at random" if args.drop else "")
+            + (f", {args.inner_iters} inner local steps" if args.inner_iters else "")
+            + (f", tensor-core update units from panel width {args.tensor_units}"
+               if args.tensor_units > 0 else ""))
+
+
 def workload_mask(args, g):
     """Presence mask [S][m] of the workload's measurement rows, or None."""
     from paper_2604_23175_gb300 import synth
@@ -543,14 +557,7 @@ def run_ours(args, dist):
     x_fp64_h = x_fp64.cpu().numpy()
     cmp.close()
 
-    variant = bool(args.workload != WORKLOAD or S != 64 or args.areas or args.family or args.drop
-                   or args.inner_iters or args.tensor_units >= 0)
-    desc = WORKLOAD_DESC if not variant else (
-        f"{g.name} x{S} snapshots" + (f", {args.family} rows dropped" if args.family else "")
-        + (f", {100 * args.drop:g}% rows dropped at random" if args.drop else "")
-        + (f", {args.inner_iters} inner local steps" if args.inner_iters else "")
-        + (f", tensor-core update units from panel width {args.tensor_units}"
-           if args.tensor_units > 0 else ""))
+    desc = workload_desc(args, g, S)
     # every kernel of the library launched inside the timed region (all legs)
     launches = sum(r["launches"] for r in rec.values())
     out = {
@@ -729,6 +736,7 @@ def run_reference(args, dist):
     if dist.rank != 0:
         return None
     hi = host_info()
+    g = workload_grid(args)
     P = max(1, min(hi["nproc"] or 1, args.snapshots))
     argv = [a for a in sys.argv[1:]]
     times = []
@@ -742,7 +750,10 @@ def run_reference(args, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "n_snap_per_step": P, "tol": TOL, "max_iter": MAX_ITER},
+            "config": {"workload": workload_desc(args, g, args.snapshots), "n_bus": g.n_bus,
+                       "n_branch": g.n_branch, "n_area": g.n_area, "n_snap": args.snapshots,
+                       "precision": "fp64 (the oracle)", "tol": TOL, "max_iter": MAX_ITER,
+                       "snapshots_solved_per_step": P, "parallelism": "one snapshot per host worker process"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": P, "kind": "oracle",
                              "sample": f"first {P} of the {args.snapshots} snapshots per step, centralised FP64 Gauss-Newton "
                                        f"(SciPy sparse LU), one snapshot per worker process"},

@@ -74,3 +74,15 @@ def test_oracle_baseline_children_use_the_workload_mask():
     full = wls.gauss_newton(net, z, wls.weights(sig), tol=bench.TOL, max_iter=bench.MAX_ITER)
     assert np.max(np.abs(x[0] - np.concatenate([ref.Vm, ref.Va]))) < 1e-12
     assert np.max(np.abs(x[0] - np.concatenate([full.Vm, full.Va]))) > 1e-6
+
+
+def test_workload_name_is_shared_by_both_arms():
+    """The GPU arm and the oracle's reference arm name the same workload: the
+    benchmark's own description by default, a variant's flags otherwise."""
+    args = bench.parse_from([])
+    g = synth.make_grid(bench.WORKLOAD)
+    assert bench.workload_desc(args, g, args.snapshots) == bench.WORKLOAD_DESC
+    v = bench.parse_from(["--areas", "16", "--drop", "0.1"])
+    d = bench.workload_desc(v, g, v.snapshots)
+    assert d != bench.WORKLOAD_DESC and "10% rows dropped" in d
+    assert bench.workload_desc(args, g, 16) != bench.WORKLOAD_DESC
