@@ -79,6 +79,17 @@ def test_symbolic_setup_selfcheck(mase, name, slack_b):
     assert np.all(err < 1e-12), err
 
 
+@pytest.mark.parametrize("name,K", [("grid10000_k48", 0), ("grid9241_k32", 16), ("grid9241_k32", 48)])
+def test_symbolic_setup_selfcheck_other_partitions(mase, name, K):
+    """The 10000-bus grid and the benchmark network split by the partitioner
+    into other numbers of areas (the area-count sweep's inputs)."""
+    g = synth.make_grid(name)
+    if K:
+        g = synth.partition_network(g, K)
+    err = mase.selfcheck(g, seed=3)
+    assert np.all(err < 1e-12), err
+
+
 def test_selfcheck_tiny_and_single_area(mase):
     g = tiny_grid(12, 3, seed=5)
     assert np.all(mase.selfcheck(g, 1) < 1e-12)
