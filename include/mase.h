@@ -236,14 +236,22 @@ int mase_set_measurements(mase_handle *h, const mase_measurements *meas);
 int mase_solve(mase_handle *h, const double *x0, double tol, int32_t max_iter,
                double *x_out, mase_stats *stats);
 
-/* Evaluate h(x) for n_snap states x[n_snap][2N] into z_out[n_snap][m]
- * (canonical order).  Uses the handle's network; x and z_out host or device. */
+/* Evaluate h(x) (Eq. typed_meas: voltage magnitudes, injections and flows
+ * at both ends under the pi model) for n_snap states x[n_snap][2N]
+ * (Vm then Va per snapshot) into z_out[n_snap][m] (canonical order).  Uses
+ * the handle's network; n_snap is independent of the handle's batch size;
+ * x and z_out host or device.  Errors: MASE_EINVAL (NULL pointers,
+ * n_snap < 1), MASE_EDEVICE. */
 int mase_measure(mase_handle *h, const double *x, int32_t n_snap, double *z_out);
 
-/* Structural information filled by mase_create. */
+/* Copy the structural information and autotuner choices filled by
+ * mase_create into *info.  MASE_EINVAL for NULL arguments. */
 int mase_get_info(const mase_handle *h, mase_info *info);
 
-/* Choose the start mode used by mase_solve when x0 is NULL. */
+/* Choose the start mode used by mase_solve when x0 is NULL: MASE_START_FLAT
+ * (or MASE_START_X0, which then also means flat) or MASE_START_LEARNED (a
+ * later mase_solve returns MASE_ENOTREADY if no model is trained or loaded).
+ * MASE_EINVAL for a NULL handle or another value. */
 int mase_set_start_mode(mase_handle *h, int32_t start_mode);
 
 /* Host-only: run the one-time symbolic setup of mase_create (Sec. 4.1, 4.3)
@@ -338,11 +346,15 @@ int mase_warmstart_train(mase_handle *h, const double *z, const uint8_t *mask, c
                          int32_t n, const mase_warmstart_options *opt, double *final_loss);
 
 /* The networks' proposal x_out[n_snap][2N] for the handle's current
- * measurements (slack angle 0), without Gauss-Newton.  x_out host or device. */
+ * measurements (slack angle 0), without Gauss-Newton.  x_out host or device.
+ * MASE_ENOTREADY without a model or measurements, MASE_EINVAL for NULL
+ * arguments, MASE_EDEVICE. */
 int mase_warmstart_predict(mase_handle *h, double *x_out);
 
 /* Save / load the trained networks (weights and normalisation) to a file; a
- * loaded file must match the handle's network and partition. */
+ * loaded file must match the handle's network and partition.  MASE_EINVAL for
+ * NULL arguments, a file that cannot be opened, is not a warm-start file or
+ * does not match; save returns MASE_ENOTREADY without a model. */
 int mase_warmstart_save(const mase_handle *h, const char *path);
 int mase_warmstart_load(mase_handle *h, const char *path);
 
@@ -350,7 +362,9 @@ int mase_warmstart_load(mase_handle *h, const char *path);
  * kernels, for checking gradients: dims[5] = {d_in, H, H, H, d_out}
  * (n_layers = 4, H a multiple of 8); params packs W_l[out][in] then b_l for
  * l = 1..4 (FP32, host); X[batch][d_in], T[batch][d_out] (host).  loss gets
- * mean((Y - T)^2); grads has the layout of params. */
+ * mean((Y - T)^2); grads has the layout of params.  MASE_EINVAL unless
+ * n_layers = 4, batch >= 1 and the hidden widths are equal multiples of 8;
+ * MASE_EDEVICE (including a tensor-core wait that ran out). */
 int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const float *params,
                    const float *X, const float *T, float *loss, float *grads);
 
@@ -361,13 +375,20 @@ int mase_mlp_check(const int32_t *dims, int32_t n_layers, int32_t batch, const f
  * eps = 1e-8 as in training; per step t: m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, w <- w (1 - lr wd) - lr (m / (1-b1^t)) /
  * (sqrt(v / (1-b2^t)) + eps).  m_out, v_out (FP32) and w_bf16_out (the BF16
- * copy the networks compute with, as raw bits) may be NULL. */
+ * copy the networks compute with, as raw bits) may be NULL.  MASE_EINVAL for
+ * n < 1, steps < 1 or NULL lr, grads or w; MASE_EDEVICE. */
 int mase_adamw_check(int64_t n, int32_t steps, const float *lr, float weight_decay,
                      const float *grads, float *w, float *m_out, float *v_out,
                      uint16_t *w_bf16_out);
 
+/* Free the handle and every device buffer it owns (NULL is a no-op). */
 void mase_destroy(mase_handle *h);
+/* Name of a status code ("MASE_OK", "MASE_EINVAL", ...; "MASE_UNKNOWN" for
+ * any other value); static storage. */
 const char *mase_status_str(int code);
+/* Message of the last failure on this thread of a call other than
+ * mase_analyze and mase_selfcheck (those use mase_analyze_error); thread-local
+ * storage, valid until the next failing call on the thread. */
 const char *mase_last_error(void);
 
 #ifdef __cplusplus
