@@ -231,8 +231,16 @@ int mase_set_measurements(mase_handle *h, const mase_measurements *meas);
  * the handle's start mode: x0 (n_snap x 2N) is used when non-NULL, otherwise
  * a flat start (or the learned start after mase_set_start_mode).  Stops a
  * snapshot once max|dx| < tol (the step is applied) or after max_iter steps.
- * x_out (n_snap x 2N) receives the estimates.  Returns MASE_OK,
- * MASE_NOT_CONVERGED, or an error; per-snapshot details go to stats. */
+ * x_out (n_snap x 2N) receives the estimates.  Each Gauss-Newton step is the
+ * condensed step of Eqs. block_normal, schur_defs, global_assembly and
+ * backsub, equal to the centralised step of Eq. gn_normal.  Per-snapshot
+ * results go to stats.  The return value is the code of the worst snapshot:
+ * MASE_EDEVICE (a bounded device-side wait gave up), else MASE_EUNOBSERVABLE
+ * (a non-positive pivot), else MASE_ENONFINITE, else MASE_NOT_CONVERGED
+ * (max_iter reached), else MASE_OK.  Other errors: MASE_EINVAL (NULL handle,
+ * max_iter outside 1..1000, tol < 0 or NaN), MASE_ENOTREADY (no measurements,
+ * or a learned start without a model), MASE_EDEVICE (a CUDA error, or a
+ * tensor-core wait of the learned start that ran out). */
 int mase_solve(mase_handle *h, const double *x0, double tol, int32_t max_iter,
                double *x_out, mase_stats *stats);
 

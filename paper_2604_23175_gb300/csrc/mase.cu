@@ -938,13 +938,19 @@ int solve_impl(mase_handle *h, const double *x0, double tol, int max_iter, doubl
     }
     if (h->opt.profile)
         for (int i = 0; i < 4; ++i) acc[i] = ev_acc[i];
-    int ret = MASE_OK;
+    // the batch's code is that of its worst snapshot, whatever their order:
+    // a device wait that gave up, then a non-positive pivot, then a
+    // non-finite step, then the iteration cap
+    int worst = 0;
     for (int s = 0; s < nS; ++s) {
-        if (status[s] == MASE_SNAP_MAX_ITER && ret == MASE_OK) ret = MASE_NOT_CONVERGED;
-        if (status[s] == MASE_SNAP_NOT_SPD) ret = MASE_EUNOBSERVABLE;
-        if (status[s] == MASE_SNAP_NONFINITE && ret != MASE_EUNOBSERVABLE) ret = MASE_ENONFINITE;
-        if (status[s] == MASE_SNAP_DEVICE) ret = MASE_EDEVICE;
+        const int st = status[s];
+        const int rank = st == MASE_SNAP_DEVICE ? 4 : st == MASE_SNAP_NOT_SPD ? 3
+                       : st == MASE_SNAP_NONFINITE ? 2 : st == MASE_SNAP_MAX_ITER ? 1 : 0;
+        worst = std::max(worst, rank);
     }
+    static const int kRetOfRank[5] = {MASE_OK, MASE_NOT_CONVERGED, MASE_ENONFINITE, MASE_EUNOBSERVABLE,
+                                      MASE_EDEVICE};
+    const int ret = kRetOfRank[worst];
     if (stats) {
         for (int s = 0; s < nS; ++s) {
             if (stats->iters) stats->iters[s] = iters[s];

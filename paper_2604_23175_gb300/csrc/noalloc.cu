@@ -254,11 +254,12 @@ int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, int64_t n_S
         (e = cudaEventRecord(v.ev_out, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(v.user_stream, v.ev_out, 0)) != cudaSuccess)
         return fail(MASE_EDEVICE, std::string("coordinator: ") + cudaGetErrorString(e));
-    for (int s = 0; s < S; ++s) {
-        if (status[s] & 4) return fail(MASE_EDEVICE, "a bounded device-side wait gave up");
-        if (status[s] & 1) return fail(MASE_EUNOBSERVABLE, "non-positive pivot in the boundary system");
-        if (status[s] & 2) return fail(MASE_ENONFINITE, "non-finite boundary step");
-    }
+    // the worst status over all snapshots, whatever their order
+    int any = 0;
+    for (int s = 0; s < S; ++s) any |= status[s];
+    if (any & 4) return fail(MASE_EDEVICE, "a bounded device-side wait gave up");
+    if (any & 1) return fail(MASE_EUNOBSERVABLE, "non-positive pivot in the boundary system");
+    if (any & 2) return fail(MASE_ENONFINITE, "non-finite boundary step");
     return MASE_OK;
 }
 
