@@ -53,6 +53,22 @@ def tiny_grid(n_bus=10, n_area=3, seed=7, slack_on_boundary=False):
                       rng.uniform(0.0, 0.05, L), area, n_area, 0, "tiny")
 
 
+def with_parallel_branches(grid: synth.Grid) -> synth.Grid:
+    """The grid with two branches doubled by parallel lines of other
+    impedance: one inside an area, and one tie line whose copy runs in the
+    reverse orientation."""
+    area = grid.area_of_bus
+    f, t = grid.from_bus, grid.to_bus
+    tie = int(np.flatnonzero(area[f] != area[t])[0])
+    inner = int(np.flatnonzero(area[f] == area[t])[0])
+    extra = np.array([inner, tie])
+    f2 = np.r_[f, f[inner], t[tie]].astype(np.int32)
+    t2 = np.r_[t, t[inner], f[tie]].astype(np.int32)
+    return synth.Grid(grid.n_bus, f2, t2, np.r_[grid.r, 1.3 * grid.r[extra]],
+                      np.r_[grid.x, 0.9 * grid.x[extra]], np.r_[grid.b_charge, grid.b_charge[extra]],
+                      area, grid.n_area, grid.slack, grid.name + "_parallel")
+
+
 def _gn_one(args):
     net, z, w, x0, tol, max_iter, keep_steps = args
     N = net.n_bus

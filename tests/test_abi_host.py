@@ -9,7 +9,7 @@ import pytest
 
 from oracle import wls
 from paper_2604_23175_gb300 import synth
-from tests.helpers import net_of, tiny_grid
+from tests.helpers import net_of, tiny_grid, with_parallel_branches
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -88,6 +88,16 @@ def test_symbolic_setup_selfcheck_other_partitions(mase, name, K):
         g = synth.partition_network(g, K)
     err = mase.selfcheck(g, seed=3)
     assert np.all(err < 1e-12), err
+
+
+def test_selfcheck_parallel_branches(mase):
+    """Parallel lines (inside an area, and a tie line in both orientations)
+    share gain entries and boundary unknowns."""
+    for g in (with_parallel_branches(tiny_grid(14, 3, seed=5)),
+              with_parallel_branches(synth.make_grid("grid300_k4"))):
+        info = mase.analyze(g)
+        assert info["n_meas"] == 3 * g.n_bus + 4 * g.n_branch
+        assert np.all(mase.selfcheck(g, 3) < 1e-12)
 
 
 def test_selfcheck_tiny_and_single_area(mase):

@@ -10,7 +10,7 @@ import pytest
 
 from oracle import wls
 from paper_2604_23175_gb300 import synth
-from tests.helpers import net_of, problem
+from tests.helpers import net_of, problem, with_parallel_branches
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +67,26 @@ def test_measure_matches_oracle(mase):
     for s in range(3):
         h = wls.measure(net, Vm[s], Va[s])
         assert np.max(np.abs(out[s] - h)) <= 1e-11 * max(1.0, np.max(np.abs(h)))
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_parity_parallel_branches(mase, precision):
+    """Parallel lines (one inside an area, one tie line doubled in the
+    reverse orientation): h(x) and the converged estimates equal the
+    oracle's, and FP64 takes its iteration counts."""
+    g = with_parallel_branches(synth.make_grid("grid300_k4"))
+    net, Vm, Va, z, sig = problem(g, 2, 3250)
+    est = mase.Estimator(g, sig, 2, z=z)
+    out = np.zeros_like(z)
+    est.measure(np.ascontiguousarray(np.concatenate([Vm, Va], axis=1)), out)
+    est.close()
+    for s in range(2):
+        h = wls.measure(net, Vm[s], Va[s])
+        assert np.max(np.abs(out[s] - h)) <= 1e-11 * max(1.0, np.max(np.abs(h)))
+    w = wls.weights(sig)
+    x, res = _run(mase, g, sig, z, precision=getattr(mase, precision), schedule=mase.BATCHED)
+    assert res.rc == mase.MASE_OK, (res.rc, res.status)
+    _check(net, g, x, res, z, w, range(2), same_iters=(precision == "FP64"))
 
 
 @pytest.mark.parametrize("precision", ["FP64", "MIXED"])

@@ -11,7 +11,7 @@ import scipy.optimize as so
 
 from oracle import wls
 from paper_2604_23175_gb300 import synth
-from tests.helpers import net_of, problem, tiny_grid
+from tests.helpers import net_of, problem, tiny_grid, with_parallel_branches
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")
 
@@ -88,8 +88,11 @@ def test_flat_start_closed_form():
     np.testing.assert_allclose(Qt, -0.5 * net.b_charge, atol=1e-13)
 
 
-def test_measurements_match_complex_power_flow():
+@pytest.mark.parametrize("parallel", [False, True])
+def test_measurements_match_complex_power_flow(parallel):
     grid = synth.make_grid("grid300_k4")
+    if parallel:
+        grid = with_parallel_branches(grid)
     net = net_of(grid)
     Vm, Va = synth.make_states(grid, 1, 11)
     h = wls.measure(net, Vm[0], Va[0])
