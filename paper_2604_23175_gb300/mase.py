@@ -243,6 +243,23 @@ def check_noalloc_args(need: tuple, S_blocks, b_blocks, dx_gamma) -> None:
             raise ValueError(f"{name} has {_numel(t)} elements, the handle needs {n}")
 
 
+_DTYPES = {"float64": ("torch.float64", "float64"), "uint8": ("torch.uint8", "uint8")}
+
+
+def check_array(name: str, a, n: int, dtype: str) -> None:
+    """Rejects (ValueError) an array or tensor whose element type is not
+    ``dtype`` ("float64" or "uint8") or whose element count is not ``n``,
+    before anything is passed to the library, which reads and writes these
+    buffers at the sizes the handle implies.  None passes."""
+    if a is None:
+        return
+    dt = str(getattr(a, "dtype", ""))
+    if dt not in _DTYPES[dtype]:
+        raise ValueError(f"{name} must be {dtype}, got {dt or type(a).__name__}")
+    if _numel(a) != n:
+        raise ValueError(f"{name} has {_numel(a)} elements, {n} expected")
+
+
 @dataclass
 class SolveResult:
     rc: int
@@ -264,8 +281,13 @@ class Estimator:
                  schedule=BATCHED, use_graph=True, refine=1, threads=0, device=0, stream=None,
                  profile=False, wait_polls=0, inner_iters=0, autotune=True, tensor_units=-1):
         self.lib = load()
+        m = int(grid.n_meas)
+        check_array("z", z, int(n_snap) * m, "float64")
+        check_array("mask", mask, int(n_snap) * m, "uint8")
         net, part, keep = _network(grid)
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        if sig.size != m:
+            raise ValueError(f"sigma has {sig.size} elements, {m} expected")
         opt = default_options()
         opt.precision, opt.schedule, opt.use_graph = precision, schedule, int(bool(use_graph))
         opt.refine, opt.threads, opt.device = refine, threads, device
@@ -298,6 +320,8 @@ class Estimator:
             pass
 
     def set_measurements(self, z, mask=None):
+        check_array("z", z, self.n_snap * self.n_meas, "float64")
+        check_array("mask", mask, self.n_snap * self.n_meas, "uint8")
         meas = Measurements(self.n_snap, _ptr(z), None, _ptr(mask))
         rc = self.lib.mase_set_measurements(self.h, C.byref(meas))
         if rc != MASE_OK:
@@ -311,6 +335,8 @@ class Estimator:
     def solve(self, x0=None, tol=1e-8, max_iter=10, x_out=None, check=True) -> SolveResult:
         """Solve the batch.  x_out: host array or CUDA tensor [n_snap, 2N]."""
         S = self.n_snap
+        check_array("x0", x0, S * 2 * self.n_bus, "float64")
+        check_array("x_out", x_out, S * 2 * self.n_bus, "float64")
         iters = np.zeros(S, dtype=np.int32)
         status = np.zeros(S, dtype=np.int32)
         J = np.zeros(S)
@@ -325,6 +351,8 @@ class Estimator:
 
     def measure(self, x, z_out, n_snap=None):
         n = self.n_snap if n_snap is None else n_snap
+        check_array("x", x, int(n) * 2 * self.n_bus, "float64")
+        check_array("z_out", z_out, int(n) * self.n_meas, "float64")
         rc = self.lib.mase_measure(self.h, _ptr(x), int(n), _ptr(z_out))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())
@@ -350,6 +378,8 @@ class Estimator:
         if mask is not None:
             if tuple(mask.shape) != tuple(z.shape) or "uint8" not in str(mask.dtype):
                 raise ValueError("mask must be uint8 with the shape of z")
+        check_array("z", z, int(z.shape[0]) * self.n_meas, "float64")
+        check_array("x", x, int(z.shape[0]) * 2 * self.n_bus, "float64")
         o = WarmstartOptions()
         self.lib.mase_warmstart_default_options(C.byref(o))
         o.hidden, o.epochs, o.batch, o.lr, o.weight_decay, o.seed = hidden, epochs, batch, lr, weight_decay, seed
@@ -362,6 +392,7 @@ class Estimator:
         return loss.value
 
     def warmstart_predict(self, x_out):
+        check_array("x_out", x_out, self.n_snap * 2 * self.n_bus, "float64")
         rc = self.lib.mase_warmstart_predict(self.h, _ptr(x_out))
         if rc != MASE_OK:
             raise MaseError(rc, _last_error())

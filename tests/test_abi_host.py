@@ -151,3 +151,41 @@ def test_noalloc_argument_checks_on_host(mase):
         f32[i] = np.zeros(need[i], dtype=np.float32)
         with pytest.raises(ValueError):
             mase.check_noalloc_args(need, *f32)
+
+
+def test_array_checks_before_any_library_call(mase):
+    """Per-snapshot buffers of another element type or size are refused by
+    the binding before it calls the library (which would read or write them
+    at the sizes the handle implies).  The handle below is never created: a
+    method that reached the library would fail with MaseError instead."""
+    import torch
+    g = synth.make_grid("grid300_k4")
+    S, N, m = 2, g.n_bus, g.n_meas
+    mase.check_array("x", np.zeros(S * 2 * N), S * 2 * N, "float64")
+    mase.check_array("x", torch.zeros(S, 2 * N, dtype=torch.float64), S * 2 * N, "float64")
+    mase.check_array("mask", np.ones((S, m), dtype=np.uint8), S * m, "uint8")
+    mase.check_array("x", None, S * 2 * N, "float64")
+    for bad in (np.zeros(S * 2 * N - 1), np.zeros(S * 2 * N, dtype=np.float32),
+                torch.zeros(S, 2 * N, dtype=torch.float32), [0.0] * (S * 2 * N)):
+        with pytest.raises(ValueError):
+            mase.check_array("x", bad, S * 2 * N, "float64")
+    with pytest.raises(ValueError):
+        mase.check_array("mask", np.ones((S, m), dtype=bool), S * m, "uint8")
+
+    est = mase.Estimator.__new__(mase.Estimator)
+    est.lib, est.h, est.n_snap, est.n_bus, est.n_meas = mase.load(), None, S, N, m
+    x_ok, z_ok = np.zeros((S, 2 * N)), np.zeros((S, m))
+    x_short, z_f32 = np.zeros((S, 2 * N - 1)), np.zeros((S, m), dtype=np.float32)
+    calls = [lambda: est.solve(x_out=x_short), lambda: est.solve(x0=x_short, x_out=x_ok),
+             lambda: est.measure(x_short, z_ok), lambda: est.measure(x_ok, z_f32),
+             lambda: est.set_measurements(z_f32), lambda: est.set_measurements(z_ok, np.ones((S, m))),
+             lambda: est.warmstart_predict(x_short),
+             lambda: est.warmstart_train(z_ok, x_short), lambda: est.warmstart_train(z_f32, x_ok)]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
+    sig = synth.sigma_vector(g.n_bus, g.n_branch)
+    with pytest.raises(ValueError):
+        mase.Estimator(g, sig[:-1], S)
+    with pytest.raises(ValueError):
+        mase.Estimator(g, sig, S, z=z_ok[:1])
