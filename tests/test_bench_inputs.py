@@ -86,3 +86,27 @@ def test_workload_name_is_shared_by_both_arms():
     d = bench.workload_desc(v, g, v.snapshots)
     assert d != bench.WORKLOAD_DESC and "10% rows dropped" in d
     assert bench.workload_desc(args, g, 16) != bench.WORKLOAD_DESC
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU) prints
+    one JSON line with the GPU arm's metric, unit and direction, a
+    cpu_baseline describing the run and an e2e entry without copies."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "grid300_k4", "--snapshots", "4", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(s) for s in out.stdout.splitlines() if s.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["n_bus"] == 300 and d["config"]["n_snap"] == 4
+    assert d["config"]["workload"] == "grid300_k4 x4 snapshots"
