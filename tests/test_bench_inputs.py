@@ -7,6 +7,7 @@ import os
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
@@ -110,3 +111,19 @@ def test_reference_arm_prints_the_contract_line():
                         "d2h_bytes_per_step": 0}
     assert d["config"]["n_bus"] == 300 and d["config"]["n_snap"] == 4
     assert d["config"]["workload"] == "grid300_k4 x4 snapshots"
+
+
+def test_headline_roofline_against_the_derived_alu_peak():
+    """The dominant kernel's roofline: achieved FP64 rate over the peak
+    derived from SMs, FP64 FMAs per SM cycle and the maximum SM clock, with
+    the measured DGEMM as a second denominator."""
+    peak, src = bench.fp64_alu_peak_tflops()
+    mhz = float(src.split(" x ")[-1].split()[0])
+    assert peak == pytest.approx(152 * 2 * 2 * mhz * 1e-6)
+    assert 1.0 < peak < 1.5                      # GB300 nominal FP64: 1.25 TFLOP/s
+    lo = {"fp64_tflops": 0.05, "avg_launch_ms": 2.9}
+    r = bench.headline_roofline(lo, peak, src, 1.1, 1.2e8)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] == 1.2e8
+    assert r["frac"] == pytest.approx(0.05 / peak) and r["frac_of_measured_dgemm"] == pytest.approx(0.05 / 1.1)
+    for k in ("achieved", "peak", "frac", "traffic"):
+        assert k in r
