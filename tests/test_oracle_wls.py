@@ -198,6 +198,39 @@ def test_schur_step_equals_dense_solve_on_tiny_grid(slack_on_boundary):
     assert np.max(np.abs(dx - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
+def test_schur_blocks_match_the_block_inverse():
+    """Per area, the condensed pair of Eq. schur_defs against the block
+    inverse of the local system.  An area without the slack has a singular
+    local gain matrix (a common shift of its angles leaves its rows
+    unchanged), so the boundary block is shifted by D = d I first: the local
+    matrix G_k' = [[G_ii, G_ib], [G_bi, G_bb + D]] is then SPD, its Schur
+    complement is S_b + D and its condensed rhs is b_hat_b, so
+    (S_b + D)^{-1} is the boundary block of G_k'^{-1} and
+    (S_b + D)^{-1} b_hat_b the boundary part of G_k'^{-1} [b_i; b_b]."""
+    grid = synth.make_grid("grid300_k4")
+    net, Vm, Va, z, sig = problem(grid, 1, 2450)
+    w = wls.weights(sig)
+    part = wls.partition(net, grid.area_of_bus, grid.n_area)
+    vm, va = Vm[0] * 1.01, Va[0] * 0.9
+    H = wls.jacobian(net, vm, va)
+    r = z[0] - wls.measure(net, vm, va)
+    for k in range(grid.n_area):
+        blk = wls.area_blocks(H, w, r, part, k)
+        Sb, bh = wls.schur_condense(blk)
+        ni, nb = blk.Gii.shape[0], blk.Gbb.shape[0]
+        D = np.mean(np.diag(blk.Gbb)) * np.eye(nb)
+        Gk = np.block([[blk.Gii, blk.Gib], [blk.Gib.T, blk.Gbb + D]])
+        inv = np.linalg.inv(Gk)
+        ref = np.linalg.inv(inv[ni:, ni:])
+        scale = np.max(np.abs(ref))
+        np.testing.assert_allclose(Sb + D, ref, rtol=0, atol=1e-9 * scale)
+        np.testing.assert_allclose(Sb, Sb.T, rtol=0, atol=1e-12 * scale)
+        assert np.min(np.linalg.eigvalsh(Sb)) >= -1e-9 * scale     # positive semi-definite
+        sol = inv @ np.concatenate([blk.bi, blk.bb])
+        np.testing.assert_allclose(np.linalg.solve(Sb + D, bh), sol[ni:], rtol=0,
+                                   atol=1e-9 * np.max(np.abs(sol)))
+
+
 def test_area_blocks_sum_to_global_gain():
     """sum_k E_k^T G_k E_k (lifted to the global unknowns) equals G entrywise,
     and every unknown is internal to exactly one area or on the boundary."""
