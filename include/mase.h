@@ -329,7 +329,8 @@ int mase_coordinator_noalloc(mase_handle *h, const double *S_blocks, int64_t n_S
  * keeps the proposal per snapshot only where its objective J is below the
  * flat start's, so Gauss-Newton has the last word on the proposal. */
 typedef struct {
-    int32_t  hidden;        /* width of the three hidden layers, multiple of 8 (512)   */
+    int32_t  hidden;        /* width of the three hidden layers, a multiple of 8 in
+                               8..8192 (512)                                           */
     int32_t  epochs;        /* passes over the training set                            */
     int32_t  batch;         /* samples per AdamW step, multiple of 8                   */
     float    lr;            /* peak learning rate (cosine decay to 5 %)                 */

@@ -691,6 +691,11 @@ void destroy_warmstart(WarmStart *w) { delete w; }
 namespace {
 
 // layout of the per-area networks over the handle's areas
+// hidden widths the networks may have: multiples of 8 (the GEMM operand
+// rows are 16-byte aligned) up to kMaxHidden
+constexpr int kMaxHidden = 8192;
+bool hidden_ok(int hidden) { return hidden >= 8 && hidden <= kMaxHidden && hidden % 8 == 0; }
+
 int build_layout(mase_handle *h, WarmStart &W, int hidden) {
     const mase::Setup &S = h->S;
     W.K = S.K;
@@ -1091,7 +1096,7 @@ int mase_warmstart_train(mase_handle *h, const double *z, const uint8_t *mask, c
     if (opt_in) opt = *opt_in;
     else mase_warmstart_default_options(&opt);
     if (n < 8 || opt.batch < 8 || opt.batch % 8 || opt.batch > n || opt.epochs < 1 ||
-        opt.hidden < 8 || opt.hidden % 8 || !(opt.lr > 0.f))
+        !hidden_ok(opt.hidden) || !(opt.lr > 0.f))
         return fail(MASE_EINVAL, "bad warm-start training arguments");
     if (cudaSetDevice(h->opt.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice");
     cudaStream_t st = h->stream;
@@ -1314,6 +1319,7 @@ int mase_warmstart_load(mase_handle *h, const char *path) {
     if (!f || std::memcmp(magic, "MASEWS01", 8)) return fail(MASE_EINVAL, "not a warm-start file");
     int32_t hdr[4];
     f.read((char *)hdr, sizeof(hdr));
+    if (!f || !hidden_ok(hdr[1])) return fail(MASE_EINVAL, "not a warm-start file");
     if (cudaSetDevice(h->opt.device) != cudaSuccess) return fail(MASE_EDEVICE, "cudaSetDevice");
     WarmStart *W = new WarmStart();
     int rc = build_layout(h, *W, hdr[1]);
