@@ -29,7 +29,8 @@ def _connected(grid, k):
     return len(seen) == len(members)
 
 
-@pytest.mark.parametrize("name,K", [("grid2869_k16", 6), ("grid2869_k16", 16), ("grid9241_k32", 24)])
+@pytest.mark.parametrize("name,K", [("grid2869_k16", 6), ("grid2869_k16", 16), ("grid9241_k32", 2),
+                                    ("grid9241_k32", 4), ("grid9241_k32", 24)])
 def test_partition_covers_connected_and_deterministic(name, K):
     g = synth.make_grid(name)
     p = synth.partition_network(g, K, seed=3)
