@@ -77,6 +77,24 @@ def test_printed_objective_is_half_weighted_norm_squared():
         assert abs(half - row["objective"]) <= row["weighted_residual_norm"] * 0.005 + 0.01
 
 
+def test_printed_objective_follows_chi_square_law():
+    """Reading of the objective scale from the paper's own numbers (Sec. 5.2,
+    5.3, 5.4): for PEGASE-2869 the full row set has m = 3N + 4L rows (a flow
+    family is 4582 / m = 17.01 % of them, as printed) and n = 5737 states.
+    Twice the printed objective lies within 2 sigma of the chi-square mean
+    m - n of r^T W r at the estimate; the printed value read as r^T W r
+    itself would lie dozens of sigma away."""
+    gold = json.load(open(GOLDEN))
+    p = gold["pegase2869"]
+    m = 3 * p["n_bus"] + 4 * p["n_branch"]
+    assert round(100 * p["flow_family_rows"] / m, 2) == p["flow_family_fraction_percent"]
+    dof = m - p["n_state"]
+    sd = np.sqrt(2 * dof)
+    obj = [r for r in gold["solution_agreement"] if r["case"] == "PEGASE-2869"][0]["objective"]
+    assert abs(2 * obj - dof) < 2 * sd
+    assert abs(obj - dof) > 20 * sd
+
+
 def test_flat_start_closed_form():
     """V = 1, theta = 0: P_ij = g - g = 0 and Q_ij = -b_c / 2 at both ends."""
     grid = synth.make_grid("grid300_k4")
