@@ -189,3 +189,25 @@ def test_array_checks_before_any_library_call(mase):
         mase.Estimator(g, sig[:-1], S)
     with pytest.raises(ValueError):
         mase.Estimator(g, sig, S, z=z_ok[:1])
+
+
+def test_product_path_fails_loudly_without_its_library_or_gpu(tmp_path):
+    """There is no CPU path: the binding raises when the library is absent,
+    and the benchmark's own arm exits with an error when no GPU is present."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2604_23175_gb300 import mase\n"
+            "mase.LIB_PATH = %r\n"
+            "try:\n    mase.load()\nexcept RuntimeError as e:\n    print('raised', e)\n") % (
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), str(tmp_path / "absent.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.startswith("raised"), out.stdout + out.stderr
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        return
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode != 0 and "needs a CUDA device" in (out.stdout + out.stderr)
+    assert not any(s.startswith("{") for s in out.stdout.splitlines())
